@@ -13,8 +13,8 @@ Recipes (the paper names no dataset; these stand in for real DEMs):
   eps=1e-3 m so every interior cell has a strictly lower neighbour and every
   descent path reaches the grid edge (the paper assumes pits and flats have
   been removed, "The Algorithm", first paragraph).
-* ``plane``: z = 0.05*(H-1-i) + 0.02*(W-1-j) + U(-0.01, 0.01) m, then the same
-  fill.
+* ``plane``: z = 0.05*(H-1-i) + 0.02*(W-1-j) + 0.01 + U(-0.01, 0.01) m, then the
+  same fill.
 * ``serpentine_dirs``: a boustrophedon direction field, one path of H*W cells.
 * ``serpentine_dem``: a realisable serpentine (channels on odd rows, ridges on
   even rows), one path of roughly H*W/2 cells.

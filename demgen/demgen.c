@@ -112,13 +112,14 @@ int demgen_fractal(float* z, int64_t H, int64_t W, uint64_t seed, double rough, 
   return 0;
 }
 
-/* Tilted plane z = sy*(H-1-i) + sx*(W-1-j) + U(-noise, noise). */
+/* Tilted plane z = sy*(H-1-i) + sx*(W-1-j) + noise + U(-noise, noise) (the
+ * offset keeps every elevation >= 0, as the fill requires). */
 int demgen_plane(float* z, int64_t H, int64_t W, uint64_t seed, double sy, double sx, double noise) {
   if (H < 1 || W < 1 || !z) return 1;
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < H; i++)
     for (int64_t j = 0; j < W; j++)
-      z[i * W + j] = (float)(sy * (double)(H - 1 - i) + sx * (double)(W - 1 - j) +
+      z[i * W + j] = (float)(sy * (double)(H - 1 - i) + sx * (double)(W - 1 - j) + noise +
                              noise * sm_sym(seed, (uint64_t)(i * W + j)));
   return 0;
 }

@@ -1,0 +1,153 @@
+/*
+ * d8.h -- C ABI of libd8, GB300 (sm_103a) D8 flow directions and up-slope area.
+ *
+ * Method: Barnes, Lehman, Mulla, "Distributed Parallel D8 Up-Slope Area
+ * Calculation in Digital Elevation Models" (PDPTA 2011).
+ *
+ * Conventions shared by every call:
+ *  - Grids are row-major: cell (i, j) of an H x W grid lives at i*ld + j,
+ *    where ld >= W is the leading dimension in ELEMENTS.  Row i grows to the
+ *    south.
+ *  - Direction codes (uint8): 0..7 = N, NE, E, SE, S, SW, W, NW; 8 = OUTLET
+ *    (a cell on the first/last row or column: it receives flow and passes none
+ *    on); 9 = SINK (no strictly lower neighbour).
+ *  - Every pointer passed to a compute call is a DEVICE pointer on the
+ *    context's device unless the parameter says "host".  The caller owns all
+ *    input and output buffers; the library never frees them.  Inputs and
+ *    outputs must not overlap.
+ *  - Compute calls are asynchronous on `stream` (a cudaStream_t, or NULL for
+ *    the legacy default stream).  Their return value reports errors the host
+ *    can see (bad arguments, allocation or launch failure).  Errors found on
+ *    the device (non-finite elevation, invalid code, cycle, timeout) are
+ *    OR-ed into the context's status word; d8_get_status() reads and clears it.
+ *  - A context owns its workspace (device arrays for the per-tile perimeter
+ *    summaries and the combine), grown lazily with cudaMalloc and reused.
+ *    Calls on one context must not run concurrently on different streams.
+ */
+#ifndef D8_H_
+#define D8_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  D8_OK = 0,
+  D8_ERR_ARG = 1,       /* bad pointer, size, leading dimension, rule or code */
+  D8_ERR_SHAPE = 2,     /* H*W too large for the output type */
+  D8_ERR_NONFINITE = 3, /* device: an elevation is NaN or infinite */
+  D8_ERR_CYCLE = 4,     /* device: the direction field contains a cycle */
+  D8_ERR_NOMEM = 5,     /* workspace allocation failed */
+  D8_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+  D8_ERR_TIMEOUT = 7    /* device: a bounded wait gave up */
+} d8_status;
+
+/* Direction rules ("The Algorithm": steepest slope, slope = drop divided by
+ * the distance between cell centres, 1 or sqrt 2; "Introduction": lowest
+ * neighbour).  Ties go to the first direction in N, NE, E, SE, S, SW, W, NW
+ * order; only a strictly positive drop counts. */
+typedef enum { D8_RULE_STEEPEST = 0, D8_RULE_LOWEST = 1 } d8_rule;
+
+typedef struct d8_ctx d8_ctx;
+typedef struct d8_batch d8_batch;
+typedef void* d8_stream; /* a cudaStream_t */
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * *ctx receives the handle.  Errors: D8_ERR_ARG (ctx NULL), D8_ERR_CUDA. */
+d8_status d8_create(d8_ctx** ctx, int device);
+
+/* Synchronise the device, free the workspace and the handle.  NULL is a no-op. */
+d8_status d8_destroy(d8_ctx* ctx);
+
+/* Tile side used by later calls: 32, 64 or 128 (default 64).  One thread
+ * block holds one T x T tile (the paper's "slave partition") in shared
+ * memory.  D8_ERR_ARG for any other value. */
+d8_status d8_set_tile(d8_ctx* ctx, int tile);
+
+/* D8 flow direction of every cell ("The Algorithm"; "Introduction").
+ * z: H x W fp32 elevations (ld ldz); dir: H x W codes (ld lddir).
+ * Non-finite z sets D8_ERR_NONFINITE in the status word and gives that cell
+ * SINK.  Errors: D8_ERR_ARG. */
+d8_status d8_flowdir(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, uint8_t* dir,
+                     int64_t lddir, d8_rule rule, d8_stream stream);
+
+/* Unit up-slope area A(p) = 1 + sum of A over the cells draining into p
+ * (Eq. 1, section "Up-Slope Area"), computed with the paper's partition
+ * scheme: per-tile internal areas with unknown inflows (Algorithms 1-4), a
+ * device solve of the tile-perimeter link graph (Algorithms 5-6) and a
+ * finalising pass per tile (Algorithms 7-8).
+ * dir: H x W codes (any field: a code 0..7 pointing off the grid, 8 and 9 end
+ * a path; codes > 9 set D8_ERR_ARG in the status word; a cycle sets
+ * D8_ERR_CYCLE).  A: H x W uint32 counts (ld ldA).
+ * Errors: D8_ERR_ARG, D8_ERR_SHAPE (H*W > 2^32-1), D8_ERR_NOMEM, D8_ERR_CUDA. */
+d8_status d8_accumulate(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir, uint32_t* A,
+                        int64_t ldA, d8_stream stream);
+
+/* Directions and unit counts in one pipeline: the direction stencil is fused
+ * into the first per-tile pass, so z is read once and dir written once.
+ * Same arguments and errors as d8_flowdir + d8_accumulate. */
+d8_status d8_flowdir_accumulate(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
+                                uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA, d8_stream stream);
+
+/* Weighted up-slope area A(p) = w(p) + sum of A over the cells draining into
+ * p (Eq. 1 with the paragraph after it: cells "may or may not be weighted
+ * equally").  fp32 in and out, compensated (TwoSum) fp32 accumulation
+ * throughout.  w: H x W (ld ldw); A: H x W (ld ldA).  Errors as
+ * d8_accumulate. */
+d8_status d8_accumulate_weighted(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
+                                 const float* w, int64_t ldw, float* A, int64_t ldA, d8_stream stream);
+
+/* Adjoint of d8_accumulate_weighted: for a loss L with dL/dA = dA,
+ * dw(q) = dL/dw(q) = dA(q) + dw(down-slope neighbour of q), i.e. the sum of
+ * dA over q's flow path (the transpose of Eq. 1).  Per-tile path sums, a
+ * pointer-jumping solve over the tile exits, then a finalising pass.
+ * fp32 in and out, compensated accumulation.  Errors as d8_accumulate. */
+d8_status d8_accumulate_backward(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
+                                 const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream);
+
+/* Plan a batch of n independent DEMs with the given shapes (host arrays of n
+ * entries; DEM k is H[k] x W[k], dense, ld = W[k]).  The plan owns a tile
+ * table, a workspace sized for the whole batch and (after the first run) a
+ * CUDA graph of the pipeline.  Errors: D8_ERR_ARG, D8_ERR_SHAPE, D8_ERR_NOMEM. */
+d8_status d8_batch_plan(d8_ctx* ctx, int n, const int64_t* H, const int64_t* W, d8_batch** plan);
+
+/* Directions and unit counts for every DEM of the batch: one persistent
+ * launch per pipeline stage over all tiles of all DEMs, fed by a device tile
+ * work queue.  z, dir, A: host arrays of n device pointers.  The first call
+ * captures the pipeline in a CUDA graph; later calls with the same pointers
+ * and rule replay it.  Errors as d8_flowdir_accumulate. */
+d8_status d8_batch_flowdir_accumulate(d8_batch* plan, const float* const* z, uint8_t* const* dir,
+                                      uint32_t* const* A, d8_rule rule, d8_stream stream);
+
+/* Free a plan (synchronises its stream first).  NULL is a no-op. */
+d8_status d8_batch_destroy(d8_batch* plan);
+
+/* Synchronise `stream`, read and clear the context's device status word.
+ * Returns D8_OK or the first device-side error recorded (NONFINITE, ARG,
+ * CYCLE, TIMEOUT, in that order of precedence). */
+d8_status d8_get_status(d8_ctx* ctx, d8_stream stream);
+
+/* Static text for a status code. */
+const char* d8_status_string(d8_status s);
+
+/* Per-stage device timing of the calls made while profiling is on.
+ * d8_set_profiling(ctx, 1) records CUDA events around every stage launch of
+ * the following calls.  d8_stage_times() synchronises on the last event and
+ * writes, for each stage s < max, the summed milliseconds ms[s] and the
+ * launch count launches[s] since the last reset (either may be NULL), then
+ * resets them; it returns the number of stages through *n.  Stage names come
+ * from d8_stage_name(s). */
+d8_status d8_set_profiling(d8_ctx* ctx, int on);
+d8_status d8_stage_times(d8_ctx* ctx, float* ms, int64_t* launches, int max, int* n);
+const char* d8_stage_name(int stage);
+
+/* Library version string. */
+const char* d8_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* D8_H_ */

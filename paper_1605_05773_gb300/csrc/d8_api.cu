@@ -1,0 +1,567 @@
+// d8_api.cu -- the C ABI of libd8 (declared in include/d8.h): contexts,
+// workspace, argument checks, stage timing, the forward / weighted / backward
+// pipelines and the batch plan with CUDA-graph replay.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "d8.h"
+#include "d8_internal.h"
+
+using namespace d8;
+
+namespace {
+
+enum Stage { ST_FLOWDIR = 0, ST_UP, ST_COMBINE, ST_DOWN, ST_BWD_UP, ST_BWD_COMBINE, ST_BWD_DOWN, ST_COUNT };
+const char* const kStageNames[ST_COUNT] = {"flowdir", "tile_up", "combine", "tile_down",
+                                           "bwd_tile_up", "bwd_combine", "bwd_tile_down"};
+
+struct Timing {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int bit_width(uint64_t x) {
+  int r = 0;
+  while (x) {
+    r++;
+    x >>= 1;
+  }
+  return r;
+}
+
+}  // namespace
+
+struct d8_ctx {
+  int device = 0;
+  int T = 64;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  uint32_t* status = nullptr;
+  int profiling = 0;
+  std::vector<cudaEvent_t> free_events;
+  std::vector<Timing> pending;
+  double ms[ST_COUNT] = {};
+  int64_t launches[ST_COUNT] = {};
+};
+
+struct d8_batch {
+  d8_ctx* ctx = nullptr;
+  int n = 0;
+  int T = 64;
+  std::vector<DemDesc> host_desc;
+  DemDesc* dev_desc = nullptr;
+  int32_t* dev_tile_dem = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int64_t ntiles = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int graph_rule = -1;
+  cudaStream_t graph_stream = nullptr;
+  int launches_per_run = 0;
+};
+
+namespace {
+
+d8_status cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return D8_ERR_NOMEM;
+  return e == cudaSuccess ? D8_OK : D8_ERR_CUDA;
+}
+
+cudaEvent_t get_event(d8_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII bracket of one stage: counts launches, records events when profiling
+struct StageScope {
+  d8_ctx* c;
+  int st;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int n = 0;
+  StageScope(d8_ctx* c_, int st_, cudaStream_t s_) : c(c_), st(st_), s(s_) {
+    if (c->profiling) {
+      a = get_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~StageScope() {
+    c->launches[st] += n;
+    if (c->profiling && a) {
+      cudaEvent_t b = get_event(c);
+      cudaEventRecord(b, s);
+      c->pending.push_back(Timing{st, a, b});
+    }
+  }
+};
+
+bool bad_grid(const void* p, int64_t H, int64_t W, int64_t ld) { return !p || H < 1 || W < 1 || ld < W; }
+
+// Workspace for a pipeline over `ntiles` tiles of side T with value size vbytes.
+size_t pipe_bytes(int64_t ntiles, int T, size_t vbytes) {
+  const size_t ns = (size_t)ntiles * 4 * T;
+  return align256(ns * 2) + align256(ns * vbytes) + 2 * align256(ns * 4) + 2 * align256(ns * vbytes) +
+         align256(sizeof(uint32_t) * (MAX_ROUNDS + 2)) + align256(sizeof(uint32_t) * 16);
+}
+
+Pipe carve_pipe(void* base, int64_t ntiles, int T, size_t vbytes, uint32_t* status) {
+  Pipe p{};
+  p.T = T;
+  p.ntiles = ntiles;
+  p.nslots = ntiles * 4 * T;
+  p.rounds = bit_width((uint64_t)p.nslots);
+  if (p.rounds > MAX_ROUNDS) p.rounds = MAX_ROUNDS;
+  const size_t ns = (size_t)p.nslots;
+  char* q = static_cast<char*>(base);
+  p.pex = reinterpret_cast<uint16_t*>(q);
+  q += align256(ns * 2);
+  p.pval = q;
+  q += align256(ns * vbytes);
+  p.P[0] = reinterpret_cast<uint32_t*>(q);
+  q += align256(ns * 4);
+  p.P[1] = reinterpret_cast<uint32_t*>(q);
+  q += align256(ns * 4);
+  p.S = q;
+  q += align256(ns * vbytes);
+  p.S2 = q;
+  q += align256(ns * vbytes);
+  p.flags = reinterpret_cast<uint32_t*>(q);
+  q += align256(sizeof(uint32_t) * (MAX_ROUNDS + 2));
+  p.queue = reinterpret_cast<uint32_t*>(q);
+  p.status = status;
+  return p;
+}
+
+d8_status ensure_ws(d8_ctx* c, size_t bytes) {
+  if (c->ws_bytes >= bytes) return D8_OK;
+  if (c->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  cudaError_t e = cudaMalloc(&c->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return D8_ERR_NOMEM;
+  }
+  c->ws_bytes = bytes;
+  return D8_OK;
+}
+
+DemDesc make_desc(int64_t H, int64_t W, int T) {
+  DemDesc d{};
+  d.H = H;
+  d.W = W;
+  d.ntx = (W + T - 1) / T;
+  d.nty = (H + T - 1) / T;
+  d.tile_base = 0;
+  return d;
+}
+
+DemTable single(const DemDesc& d) {
+  DemTable t{};
+  t.one = d;
+  t.ndem = 1;
+  return t;
+}
+
+bool slots_fit(int64_t ntiles, int T) { return (uint64_t)ntiles * 4 * (uint64_t)T < 0xFFFFFFF0ull; }
+
+// forward pipeline on one DEM: tile pass (with fused directions when z given),
+// combine, finalise
+d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStream_t s) {
+  const int T = c->T;
+  DemDesc d = d0;
+  const int64_t ntiles = d.ntx * d.nty;
+  if (!slots_fit(ntiles, T)) return D8_ERR_SHAPE;
+  const bool weighted = (mode == UP_WEIGHTED);
+  const size_t vb = weighted ? 8 : 4;
+  if (up_smem_bytes(T, mode) == 0 || down_smem_bytes(T, weighted) == 0) return D8_ERR_ARG;
+  d8_status st = ensure_ws(c, pipe_bytes(ntiles, T, vb));
+  if (st != D8_OK) return st;
+  Pipe p = carve_pipe(c->ws, ntiles, T, vb, c->status);
+  DemTable dt = single(d);
+  cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  {
+    StageScope sc(c, ST_UP, s);
+    e = launch_up(dt, p, mode, rule, s, &sc.n);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  {
+    StageScope sc(c, ST_COMBINE, s);
+    e = launch_combine_fwd(dt, p, weighted, s, &sc.n);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  {
+    StageScope sc(c, ST_DOWN, s);
+    e = launch_down(dt, p, weighted, s, &sc.n);
+  }
+  return cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* d8_version(void) { return "libd8 0.1 (sm_103a)"; }
+
+const char* d8_status_string(d8_status s) {
+  switch (s) {
+    case D8_OK: return "ok";
+    case D8_ERR_ARG: return "invalid argument or direction code";
+    case D8_ERR_SHAPE: return "grid too large for the output type";
+    case D8_ERR_NONFINITE: return "non-finite elevation";
+    case D8_ERR_CYCLE: return "direction field contains a cycle";
+    case D8_ERR_NOMEM: return "out of device memory";
+    case D8_ERR_CUDA: return "CUDA runtime error";
+    case D8_ERR_TIMEOUT: return "bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* d8_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : nullptr; }
+
+d8_status d8_create(d8_ctx** out, int device) {
+  if (!out) return D8_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return D8_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return D8_ERR_CUDA;
+  d8_ctx* c = new (std::nothrow) d8_ctx();
+  if (!c) return D8_ERR_NOMEM;
+  c->device = device;
+  if (cudaMalloc(&c->status, 256) != cudaSuccess || cudaMemset(c->status, 0, 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return D8_ERR_NOMEM;
+  }
+  *out = c;
+  return D8_OK;
+}
+
+d8_status d8_destroy(d8_ctx* c) {
+  if (!c) return D8_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->ws) cudaFree(c->ws);
+  if (c->status) cudaFree(c->status);
+  for (auto& t : c->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : c->free_events) cudaEventDestroy(e);
+  delete c;
+  return D8_OK;
+}
+
+d8_status d8_set_tile(d8_ctx* c, int tile) {
+  if (!c || (tile != 32 && tile != 64 && tile != 128)) return D8_ERR_ARG;
+  c->T = tile;
+  return D8_OK;
+}
+
+d8_status d8_set_profiling(d8_ctx* c, int on) {
+  if (!c) return D8_ERR_ARG;
+  c->profiling = on ? 1 : 0;
+  return D8_OK;
+}
+
+d8_status d8_stage_times(d8_ctx* c, float* ms, int64_t* launches, int max, int* n) {
+  if (!c) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  for (auto& t : c->pending) {
+    if (cudaEventSynchronize(t.b) != cudaSuccess) return D8_ERR_CUDA;
+    float x = 0.0f;
+    cudaEventElapsedTime(&x, t.a, t.b);
+    c->ms[t.stage] += x;
+    c->free_events.push_back(t.a);
+    c->free_events.push_back(t.b);
+  }
+  c->pending.clear();
+  for (int s = 0; s < ST_COUNT && s < max; s++) {
+    if (ms) ms[s] = (float)c->ms[s];
+    if (launches) launches[s] = c->launches[s];
+  }
+  for (int s = 0; s < ST_COUNT; s++) {
+    c->ms[s] = 0.0;
+    c->launches[s] = 0;
+  }
+  if (n) *n = ST_COUNT;
+  return D8_OK;
+}
+
+d8_status d8_get_status(d8_ctx* c, d8_stream stream) {
+  if (!c) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return D8_ERR_CUDA;
+  const d8_status order[] = {D8_ERR_NONFINITE, D8_ERR_ARG, D8_ERR_CYCLE, D8_ERR_TIMEOUT};
+  for (d8_status o : order)
+    if (h & (1u << o)) return o;
+  return D8_OK;
+}
+
+d8_status d8_flowdir(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, uint8_t* dir, int64_t lddir,
+                     d8_rule rule, d8_stream stream) {
+  if (!c || bad_grid(z, H, W, ldz) || bad_grid(dir, H, W, lddir) || (rule != 0 && rule != 1)) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  DemDesc d = make_desc(H, W, c->T);
+  d.z = z;
+  d.ldz = ldz;
+  d.dir = dir;
+  d.lddir = lddir;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StageScope sc(c, ST_FLOWDIR, s);
+  return cuda_fail(launch_flowdir(single(d), d.ntx * d.nty, c->T, (int)rule, c->status, s, &sc.n));
+}
+
+d8_status d8_accumulate(d8_ctx* c, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir, uint32_t* A,
+                        int64_t ldA, d8_stream stream) {
+  if (!c || bad_grid(dir, H, W, lddir) || bad_grid(A, H, W, ldA)) return D8_ERR_ARG;
+  if ((uint64_t)H * (uint64_t)W > 0xFFFFFFFFull) return D8_ERR_SHAPE;
+  cudaSetDevice(c->device);
+  DemDesc d = make_desc(H, W, c->T);
+  d.dir = const_cast<uint8_t*>(dir);
+  d.lddir = lddir;
+  d.A = A;
+  d.ldA = ldA;
+  return run_forward(c, d, UP_UNIT_DIR, 0, static_cast<cudaStream_t>(stream));
+}
+
+d8_status d8_flowdir_accumulate(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
+                                uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA, d8_stream stream) {
+  if (!c || bad_grid(z, H, W, ldz) || bad_grid(dir, H, W, lddir) || bad_grid(A, H, W, ldA) ||
+      (rule != 0 && rule != 1))
+    return D8_ERR_ARG;
+  if ((uint64_t)H * (uint64_t)W > 0xFFFFFFFFull) return D8_ERR_SHAPE;
+  cudaSetDevice(c->device);
+  DemDesc d = make_desc(H, W, c->T);
+  d.z = z;
+  d.ldz = ldz;
+  d.dir = dir;
+  d.lddir = lddir;
+  d.A = A;
+  d.ldA = ldA;
+  return run_forward(c, d, UP_UNIT_Z, (int)rule, static_cast<cudaStream_t>(stream));
+}
+
+d8_status d8_accumulate_weighted(d8_ctx* c, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
+                                 const float* w, int64_t ldw, float* A, int64_t ldA, d8_stream stream) {
+  if (!c || bad_grid(dir, H, W, lddir) || bad_grid(w, H, W, ldw) || bad_grid(A, H, W, ldA)) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  DemDesc d = make_desc(H, W, c->T);
+  d.dir = const_cast<uint8_t*>(dir);
+  d.lddir = lddir;
+  d.w = w;
+  d.ldw = ldw;
+  d.A = A;
+  d.ldA = ldA;
+  return run_forward(c, d, UP_WEIGHTED, 0, static_cast<cudaStream_t>(stream));
+}
+
+d8_status d8_accumulate_backward(d8_ctx* c, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
+                                 const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream) {
+  if (!c || bad_grid(dir, H, W, lddir) || bad_grid(dA, H, W, lddA) || bad_grid(dw, H, W, lddw)) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  const int T = c->T > 64 ? 64 : c->T;  // the path-doubling tile pass holds two buffers per cell
+  DemDesc d = make_desc(H, W, T);
+  d.dir = const_cast<uint8_t*>(dir);
+  d.lddir = lddir;
+  d.w = dA;
+  d.ldw = lddA;
+  d.A = dw;
+  d.ldA = lddw;
+  const int64_t ntiles = d.ntx * d.nty;
+  if (!slots_fit(ntiles, T)) return D8_ERR_SHAPE;
+  d8_status st = ensure_ws(c, pipe_bytes(ntiles, T, 8));
+  if (st != D8_OK) return st;
+  Pipe p = carve_pipe(c->ws, ntiles, T, 8, c->status);
+  DemTable dt = single(d);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  {
+    StageScope sc(c, ST_BWD_UP, s);
+    e = launch_bwd_up(dt, p, s, &sc.n);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  {
+    StageScope sc(c, ST_BWD_COMBINE, s);
+    e = launch_combine_bwd(dt, p, s, &sc.n);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  {
+    StageScope sc(c, ST_BWD_DOWN, s);
+    e = launch_bwd_down(dt, p, s, &sc.n);
+  }
+  return cuda_fail(e);
+}
+
+// ---------------------------------------------------------------------------
+// batch
+
+d8_status d8_batch_plan(d8_ctx* c, int n, const int64_t* H, const int64_t* W, d8_batch** out) {
+  if (!c || !out || n < 1 || !H || !W) return D8_ERR_ARG;
+  *out = nullptr;
+  cudaSetDevice(c->device);
+  d8_batch* b = new (std::nothrow) d8_batch();
+  if (!b) return D8_ERR_NOMEM;
+  b->ctx = c;
+  b->n = n;
+  b->T = c->T;
+  b->host_desc.resize(n);
+  int64_t base = 0;
+  for (int k = 0; k < n; k++) {
+    if (H[k] < 1 || W[k] < 1) {
+      delete b;
+      return D8_ERR_ARG;
+    }
+    if ((uint64_t)H[k] * (uint64_t)W[k] > 0xFFFFFFFFull) {
+      delete b;
+      return D8_ERR_SHAPE;
+    }
+    DemDesc d = make_desc(H[k], W[k], b->T);
+    d.ldz = d.lddir = d.ldA = W[k];
+    d.tile_base = base;
+    base += d.ntx * d.nty;
+    b->host_desc[k] = d;
+  }
+  b->ntiles = base;
+  if (!slots_fit(base, b->T)) {
+    delete b;
+    return D8_ERR_SHAPE;
+  }
+  std::vector<int32_t> tile_dem((size_t)base);
+  for (int k = 0; k < n; k++) {
+    const DemDesc& d = b->host_desc[k];
+    for (int64_t t = 0; t < d.ntx * d.nty; t++) tile_dem[(size_t)(d.tile_base + t)] = k;
+  }
+  b->ws_bytes = pipe_bytes(base, b->T, 4);
+  if (cudaMalloc(&b->dev_desc, sizeof(DemDesc) * n) != cudaSuccess ||
+      cudaMalloc(&b->dev_tile_dem, sizeof(int32_t) * (size_t)base) != cudaSuccess ||
+      cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    d8_batch_destroy(b);
+    return D8_ERR_NOMEM;
+  }
+  if (cudaMemcpy(b->dev_tile_dem, tile_dem.data(), sizeof(int32_t) * (size_t)base, cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    d8_batch_destroy(b);
+    return D8_ERR_CUDA;
+  }
+  *out = b;
+  return D8_OK;
+}
+
+static cudaError_t batch_enqueue(d8_batch* b, int rule, cudaStream_t s, int* n_up, int* n_comb, int* n_down) {
+  DemTable dt{};
+  dt.table = b->dev_desc;
+  dt.tile_dem = b->dev_tile_dem;
+  dt.ndem = b->n;
+  dt.one = b->host_desc[0];
+  if (b->n == 1) dt.ndem = 1;
+  Pipe p = carve_pipe(b->ws, b->ntiles, b->T, 4, b->ctx->status);
+  cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
+  if (e == cudaSuccess) e = launch_up(dt, p, UP_UNIT_Z, rule, s, n_up);
+  if (e == cudaSuccess) e = launch_combine_fwd(dt, p, false, s, n_comb);
+  if (e == cudaSuccess) e = launch_down(dt, p, false, s, n_down);
+  return e;
+}
+
+d8_status d8_batch_flowdir_accumulate(d8_batch* b, const float* const* z, uint8_t* const* dir, uint32_t* const* A,
+                                      d8_rule rule, d8_stream stream) {
+  if (!b || !z || !dir || !A || (rule != 0 && rule != 1)) return D8_ERR_ARG;
+  d8_ctx* c = b->ctx;
+  cudaSetDevice(c->device);
+  for (int k = 0; k < b->n; k++) {
+    if (!z[k] || !dir[k] || !A[k]) return D8_ERR_ARG;
+    b->host_desc[k].z = z[k];
+    b->host_desc[k].dir = dir[k];
+    b->host_desc[k].A = A[k];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the descriptor table is read by the kernels at run time, so new buffer
+  // pointers need no re-capture: upload it ahead of the graph on the stream
+  cudaError_t e = cudaMemcpyAsync(b->dev_desc, b->host_desc.data(), sizeof(DemDesc) * b->n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (b->n == 1 || !b->exec || b->graph_rule != (int)rule) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (b->graph) {
+      cudaGraphDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    if (b->n == 1) {
+      // a single DEM passes its descriptor by value: run it directly
+      int nu = 0, nc = 0, nd = 0;
+      StageScope su(c, ST_UP, s);
+      e = batch_enqueue(b, (int)rule, s, &nu, &nc, &nd);
+      su.n = nu + nc + nd;
+      return cuda_fail(e);
+    }
+    cudaStream_t cap = s;
+    bool own = false;
+    if (cap == nullptr || cap == cudaStreamLegacy || cap == cudaStreamPerThread) {
+      if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return D8_ERR_CUDA;
+      own = true;
+    }
+    int nu = 0, nc = 0, nd = 0;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = batch_enqueue(b, (int)rule, cap, &nu, &nc, &nd);
+      e = cudaStreamEndCapture(cap, &b->graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (own) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return D8_ERR_CUDA;
+    }
+    b->graph_rule = (int)rule;
+    b->launches_per_run = nu + nc + nd;
+  }
+  StageScope sc(c, ST_UP, s);
+  sc.n = b->launches_per_run;
+  return cuda_fail(cudaGraphLaunch(b->exec, s));
+}
+
+d8_status d8_batch_destroy(d8_batch* b) {
+  if (!b) return D8_OK;
+  cudaSetDevice(b->ctx->device);
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->dev_desc) cudaFree(b->dev_desc);
+  if (b->dev_tile_dem) cudaFree(b->dev_tile_dem);
+  if (b->ws) cudaFree(b->ws);
+  delete b;
+  return D8_OK;
+}
+
+}  // extern "C"

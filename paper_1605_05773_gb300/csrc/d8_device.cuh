@@ -1,0 +1,228 @@
+// d8_device.cuh -- device helpers shared by the libd8 kernels.
+//
+// Tile model (the paper's "slave partition", section "The Algorithm"): a DEM of
+// H x W cells is cut into T x T tiles (ragged at the right and bottom).  A tile
+// is held by one thread block in shared memory, cell (i, j) of the tile at
+// local index i*T + j.  The cells on a tile's border are its perimeter; each
+// perimeter cell has a fixed "slot" in a 4T-entry per-tile table:
+//   top row    (i == 0)          : slot j
+//   bottom row (i == th-1 > 0)   : slot T + j
+//   left col   (j == 0, 0<i<th-1): slot 2T + i
+//   right col  (j == tw-1 > 0, 0<i<th-1): slot 3T + i
+// so a tile's perimeter summary is a fixed-stride array and the global slot id
+// of a perimeter cell is tile * 4T + slot.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "d8_internal.h"
+
+namespace d8 {
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// ---- direction codes ----------------------------------------------------
+// 0..7 = N, NE, E, SE, S, SW, W, NW (row index grows to the south)
+__device__ __forceinline__ int code_di(int k) { return (int)((0x01222100u >> (4 * k)) & 0xFu) - 1; }
+__device__ __forceinline__ int code_dj(int k) { return (int)((0x00012221u >> (4 * k)) & 0xFu) - 1; }
+__device__ __forceinline__ int opposite(int k) { return (k + 4) & 7; }
+
+// fp32 nearest 1/sqrt(2): the diagonal distance factor of the steepest rule
+__device__ __forceinline__ float inv_sqrt2_f32() { return __uint_as_float(0x3F3504F3u); }
+
+// D8 code of an interior cell whose 3x3 neighbourhood is z[(r-1..r+1)*ld + (c-1..c+1)].
+// Steepest ("The Algorithm"): slope = drop for cardinals, drop * (1/sqrt 2) for
+// diagonals, one rounded fp32 multiply; lowest ("Introduction"): smallest z.
+// Strict comparisons in N..NW order, so the first of equal candidates wins and
+// only strictly lower neighbours count; none gives SINK (9).
+__device__ __forceinline__ int d8_code_interior(const float* z, int ld, int r, int c, int rule) {
+  const float zc = z[r * ld + c];
+  int bk = 9;
+  if (rule == 0) {
+    const float R = inv_sqrt2_f32();
+    float best = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const float zn = z[(r + code_di(k)) * ld + (c + code_dj(k))];
+      const float d = __fsub_rn(zc, zn);
+      const float s = (k & 1) ? __fmul_rn(d, R) : d;
+      if (s > best) {
+        best = s;
+        bk = k;
+      }
+    }
+  } else {
+    float best = zc;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const float zn = z[(r + code_di(k)) * ld + (c + code_dj(k))];
+      if (zn < best) {
+        best = zn;
+        bk = k;
+      }
+    }
+  }
+  return bk;
+}
+
+// ---- compensated fp32 ("float-float") ------------------------------------
+struct ff {
+  float hi, lo;
+};
+
+// Knuth TwoSum of the high parts, error terms folded in, renormalised with
+// Fast2Sum.  Explicit _rn intrinsics keep the compiler from contracting or
+// reassociating anything.
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float av = __fsub_rn(s, bv);
+  float e = __fadd_rn(__fsub_rn(a.hi, av), __fsub_rn(b.hi, bv));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, e);
+  const float lo = __fsub_rn(e, __fsub_rn(hi, s));
+  return ff{hi, lo};
+}
+
+template <class V>
+struct VOps;
+
+template <>
+struct VOps<uint32_t> {
+  static __device__ __forceinline__ uint32_t zero() { return 0u; }
+  static __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b) { return a + b; }
+  static __device__ __forceinline__ void atomic_add(uint32_t* p, uint32_t v) { atomicAdd(p, v); }
+  static __device__ __forceinline__ bool nonzero(uint32_t v) { return v != 0u; }
+};
+
+template <>
+struct VOps<ff> {
+  static __device__ __forceinline__ ff zero() { return ff{0.0f, 0.0f}; }
+  static __device__ __forceinline__ ff add(ff a, ff b) { return ff_add(a, b); }
+  // lock-free compensated add: CAS on the 64-bit (hi, lo) pair
+  static __device__ __forceinline__ void atomic_add(ff* p, ff v) {
+    unsigned long long* q = reinterpret_cast<unsigned long long*>(p);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(q);
+    for (;;) {
+      ff cur;
+      cur.hi = __uint_as_float((uint32_t)old);
+      cur.lo = __uint_as_float((uint32_t)(old >> 32));
+      const ff nv = ff_add(cur, v);
+      const unsigned long long nb =
+          (unsigned long long)__float_as_uint(nv.hi) | ((unsigned long long)__float_as_uint(nv.lo) << 32);
+      const unsigned long long prev = atomicCAS(q, old, nb);
+      if (prev == old) break;
+      old = prev;
+    }
+  }
+  static __device__ __forceinline__ bool nonzero(ff v) { return v.hi != 0.0f || v.lo != 0.0f; }
+};
+
+// DEM of a tile, by value so its fields can live in registers
+__device__ __forceinline__ DemDesc dem_of(const DemTable& t, int64_t tile) {
+  if (t.ndem == 1) return t.one;
+  return t.table[t.tile_dem[tile]];
+}
+
+__device__ __forceinline__ uint32_t* pick(uint32_t* a, uint32_t* b, int second) { return second ? b : a; }
+
+// ---- tile geometry --------------------------------------------------------
+struct TileGeo {
+  int64_t i0, j0;  // global origin
+  int th, tw;      // extent (ragged at the right/bottom)
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const DemDesc& d, int64_t local_tile, int T) {
+  TileGeo g;
+  const int64_t ty = local_tile / d.ntx, tx = local_tile % d.ntx;
+  g.i0 = ty * T;
+  g.j0 = tx * T;
+  g.th = (int)min64(T, d.H - g.i0);
+  g.tw = (int)min64(T, d.W - g.j0);
+  return g;
+}
+
+// slot of perimeter cell (i, j) of a th x tw tile, or -1 for an inner cell
+__device__ __forceinline__ int slot_of(int i, int j, int th, int tw, int T) {
+  if (i == 0) return j;
+  if (i == th - 1) return T + j;
+  if (j == 0) return 2 * T + i;
+  if (j == tw - 1) return 3 * T + i;
+  return -1;
+}
+
+// cell of slot s, or false if the slot is unused for this tile extent
+__device__ __forceinline__ bool slot_cell(int s, int th, int tw, int T, int& i, int& j) {
+  if (s < T) {
+    i = 0;
+    j = s;
+    return j < tw;
+  }
+  if (s < 2 * T) {
+    i = th - 1;
+    j = s - T;
+    return th > 1 && j < tw;
+  }
+  if (s < 3 * T) {
+    i = s - 2 * T;
+    j = 0;
+    return i >= 1 && i <= th - 2;
+  }
+  i = s - 3 * T;
+  j = tw - 1;
+  return tw > 1 && i >= 1 && i <= th - 2;
+}
+
+// Global slot id of the cell (gi, gj) of DEM d (the cell must lie on the
+// perimeter of its tile).
+__device__ __forceinline__ int64_t global_slot(const DemDesc& d, int64_t gi, int64_t gj, int T) {
+  const int64_t ty = gi / T, tx = gj / T;
+  const int i = (int)(gi - ty * T), j = (int)(gj - tx * T);
+  const int th = (int)min64(T, d.H - ty * T), tw = (int)min64(T, d.W - tx * T);
+  return (d.tile_base + ty * d.ntx + tx) * (int64_t)(4 * T) + slot_of(i, j, th, tw, T);
+}
+
+// ---- perimeter exit codes (per slot, uint16) ------------------------------
+// PEX_EXIT | k : the cell itself leaves the tile, towards direction k
+// PEX_TERM     : the cell's in-tile path ends inside the tile (outlet, sink,
+//                off-grid target)
+// otherwise    : slot of the perimeter cell where the in-tile path leaves
+constexpr uint16_t PEX_EXIT = 0x8000u;
+constexpr uint16_t PEX_TERM = 0x7FFFu;
+
+// ---- per-cell class flags in shared memory ---------------------------------
+constexpr uint8_t CL_IN = 0x08;      // target inside the tile; bits 0..2 = code
+constexpr uint8_t CL_EXIT = 0x10;    // target in another tile; bits 0..2 = code
+constexpr uint8_t CL_TERM = 0x20;    // path ends here
+constexpr uint8_t CL_ABSENT = 0x40;  // outside a ragged tile
+constexpr uint16_t JP_TERM = 0xFFFFu;
+
+// Classify a code of cell (i, j) of a tile: in-tile target, exit, or end.
+__device__ __forceinline__ uint8_t classify(int code, int i, int j, const TileGeo& g, const DemDesc& d,
+                                            uint32_t* status) {
+  if (code > 9) {
+    atomicOr(status, 1u << D8_ERR_ARG);
+    return CL_TERM;
+  }
+  if (code >= 8) return CL_TERM;
+  const int di = code_di(code), dj = code_dj(code);
+  const int64_t gi = g.i0 + i + di, gj = g.j0 + j + dj;
+  if (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) return CL_TERM;
+  const int li = i + di, lj = j + dj;
+  if (li >= 0 && lj >= 0 && li < g.th && lj < g.tw) return (uint8_t)(CL_IN | code);
+  return (uint8_t)(CL_EXIT | code);
+}
+
+__device__ __forceinline__ void set_status(uint32_t* status, int code) { atomicOr(status, 1u << code); }
+
+// Tile work queue: persistent blocks take the next tile index from a device
+// counter (zeroed before the launch) until the tiles run out.
+__device__ __forceinline__ int64_t next_tile(uint32_t* queue) {
+  __shared__ int64_t sh_tile;
+  __syncthreads();
+  if (threadIdx.x == 0) sh_tile = (int64_t)atomicAdd(queue, 1u);
+  __syncthreads();
+  return sh_tile;
+}
+
+}  // namespace d8

@@ -1,0 +1,73 @@
+// d8_internal.h -- types shared by the libd8 host code and kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "d8.h"
+
+namespace d8 {
+
+constexpr int NT = 256;                 // threads per tile block
+constexpr uint32_t ROOT = 0xFFFFFFFFu;  // "no parent" in the combine
+constexpr int MAX_ROUNDS = 40;          // pointer-jumping rounds (>= log2 of any slot count)
+
+// One DEM of a call (a single call has one; a batch has many).
+struct DemDesc {
+  const float* z;
+  int64_t ldz;
+  uint8_t* dir;
+  int64_t lddir;
+  void* A;  // uint32 counts or fp32 areas / gradients
+  int64_t ldA;
+  const float* w;  // weights (weighted) or dL/dA (backward)
+  int64_t ldw;
+  int64_t H, W;
+  int64_t ntx, nty;
+  int64_t tile_base;  // global index of this DEM's first tile
+};
+
+// The DEMs of a launch: either one descriptor passed by value, or a device
+// table plus a per-tile DEM index.
+struct DemTable {
+  DemDesc one;
+  const DemDesc* table;    // device, ndem entries (ndem > 1)
+  const int32_t* tile_dem; // device, ntiles entries (ndem > 1)
+  int ndem;
+};
+
+enum UpMode { UP_UNIT_DIR = 0, UP_UNIT_Z = 1, UP_WEIGHTED = 2 };
+
+// Device workspace of one pipeline run (all arrays indexed by global slot id
+// = tile * 4T + slot unless noted).
+struct Pipe {
+  int T;
+  int64_t ntiles, nslots;
+  int rounds;
+  uint16_t* pex;     // per slot: exit code of the in-tile path
+  void* pval;        // per slot: in-tile area at exits (fwd) / path sum (bwd)
+  uint32_t* P[2];    // combine: pointer-jumping parents (ping-pong)
+  void* S;           // combine: values (fwd: in place; bwd: ping-pong with S2)
+  void* S2;          // combine: second value buffer (bwd) / delta buffer (fwd)
+  uint32_t* flags;   // combine: per-round "still active" flags, MAX_ROUNDS+2
+  uint32_t* status;  // device status word (OR of 1 << d8_status)
+  uint32_t* queue;   // tile work-queue counters (one per stage)
+};
+
+// ---- launchers (d8_fwd.cu / d8_bwd.cu) -------------------------------------
+// Each enqueues its kernels on `s` and adds the number of kernel launches it
+// made to *nlaunch.
+cudaError_t launch_flowdir(const DemTable& dt, int64_t ntiles, int T, int rule, uint32_t* status, cudaStream_t s,
+                           int* nlaunch);
+cudaError_t launch_up(const DemTable& dt, const Pipe& p, int mode, int rule, cudaStream_t s, int* nlaunch);
+cudaError_t launch_combine_fwd(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch);
+cudaError_t launch_down(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch);
+cudaError_t launch_bwd_up(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_combine_bwd(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
+cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
+
+// shared-memory bytes of the per-tile kernels (0 = configuration unsupported)
+size_t up_smem_bytes(int T, int mode);
+size_t down_smem_bytes(int T, bool weighted);
+size_t bwd_smem_bytes(int T);
+
+}  // namespace d8

@@ -1,0 +1,114 @@
+"""Weighted up-slope area (compensated fp32) and its hand-written adjoint,
+against the fp64 oracle, the transposed solve and central differences."""
+import numpy as np
+import pytest
+import torch
+
+import demgen
+import oracle
+from tests.gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5  # max relative error against fp64
+
+
+def grad_error(g32, d_ref, c):
+    """|G32 - G64| / max(|G64|, sum over the path of |c|) (the scale-aware
+    reading of the relative error for a signed gradient)."""
+    G64 = oracle.transposed(d_ref, c.astype(np.float64))
+    scale = np.maximum(np.abs(G64), oracle.transposed(d_ref, np.abs(c).astype(np.float64)))
+    return (np.abs(g32.astype(np.float64) - G64) / scale).max(), G64
+
+
+@pytest.mark.parametrize("T", [32, 64])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (97, 131), (300, 257), (520, 130)])
+def test_weighted_and_backward_small(d8, T, shape):
+    d8.set_tile(T)
+    try:
+        H, W = shape
+        z = demgen.fractal(H, W, seed=H + 7 * W, cache=False)
+        d_ref = oracle.flowdir(z)
+        w = demgen.lognormal_weights(H, W, seed=1)
+        c = demgen.normal_cotangent(H, W, seed=2)
+        dt = to_dev(d_ref)
+        A = d8.accumulate_weighted(dt, to_dev(w)).cpu().numpy()
+        A64 = oracle.accumulate_weighted(d_ref, w.astype(np.float64))
+        assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
+        g = d8.accumulate_backward(dt, to_dev(c)).cpu().numpy()
+        err, _ = grad_error(g, d_ref, c)
+        assert err <= TOL
+        assert d8.get_status() == "OK"
+    finally:
+        d8.set_tile(64)
+
+
+def test_unit_weights_reproduce_counts(d8):
+    z = demgen.fractal(400, 333, seed=3, cache=False)
+    d_ref = oracle.flowdir(z)
+    dt = to_dev(d_ref)
+    A = d8.accumulate_weighted(dt, torch.ones((400, 333), device="cuda")).cpu().numpy()
+    np.testing.assert_array_equal(A, oracle.accumulate(d_ref).astype(np.float32))
+    # c = 1: path lengths, exactly
+    g = d8.accumulate_backward(dt, torch.ones((400, 333), device="cuda")).cpu().numpy()
+    np.testing.assert_array_equal(g, oracle.transposed(d_ref, np.ones((400, 333))).astype(np.float32))
+
+
+def test_spiral_and_serpentine_weighted(d8):
+    from tests.gpu_util import spiral_dirs
+
+    for f in (spiral_dirs(150, 170), demgen.serpentine_dirs(130, 200)):
+        H, W = f.shape
+        w = demgen.lognormal_weights(H, W, seed=5)
+        c = demgen.normal_cotangent(H, W, seed=6)
+        A = d8.accumulate_weighted(to_dev(f), to_dev(w)).cpu().numpy()
+        A64 = oracle.accumulate_weighted(f, w.astype(np.float64))
+        assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
+        g = d8.accumulate_backward(to_dev(f), to_dev(c)).cpu().numpy()
+        assert grad_error(g, f, c)[0] <= TOL
+
+
+def test_autograd_function_and_central_differences(d8):
+    H, W = 256, 192
+    z = demgen.fractal(H, W, seed=21, cache=False)
+    d_ref = oracle.flowdir(z)
+    w = demgen.lognormal_weights(H, W, seed=7)
+    c = demgen.normal_cotangent(H, W, seed=8)
+    wt = to_dev(w).requires_grad_(True)
+    A = d8.weighted_upslope(to_dev(d_ref), wt)
+    (A * to_dev(c)).sum().backward()
+    g = wt.grad.cpu().numpy()
+    err, G64 = grad_error(g, d_ref, c)
+    assert err <= TOL
+    # fp64 central differences of L(w) = sum c * A(w) (linear, so h = 1 is exact)
+    rng = np.random.default_rng(9)
+    w64, c64 = w.astype(np.float64), c.astype(np.float64)
+    for q in rng.choice(H * W, size=64, replace=False):
+        e = np.zeros(H * W)
+        e[q] = 1.0
+        e = e.reshape(H, W)
+        fd = ((c64 * oracle.accumulate_weighted(d_ref, w64 + e)).sum() -
+              (c64 * oracle.accumulate_weighted(d_ref, w64 - e)).sum()) / 2.0
+        scale = max(abs(fd), oracle.transposed(d_ref, np.abs(c64)).ravel()[q])
+        assert abs(g.ravel()[q] - fd) <= TOL * scale
+
+
+def test_8192_weighted_forward_backward(d8):
+    """8192^2 fractal, w ~ lognormal(0,1), L = sum c*A with c ~ N(0,1)."""
+    H = W = 8192
+    z = demgen.fractal(H, W)
+    d_ref = oracle.flowdir(z)
+    w = demgen.lognormal_weights(H, W, seed=11)
+    c = demgen.normal_cotangent(H, W, seed=12)
+    dt = to_dev(d_ref)
+    A = d8.accumulate_weighted(dt, to_dev(w)).cpu().numpy()
+    A64 = oracle.accumulate_weighted(d_ref, w.astype(np.float64))
+    assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
+    del A64
+    g = d8.accumulate_backward(dt, to_dev(c)).cpu().numpy()
+    err, G64 = grad_error(g, d_ref, c)
+    assert err <= TOL
+    # adjoint identity in fp64 on the GPU outputs: c.A(w) == G.w
+    lhs = float((c.astype(np.float64) * A.astype(np.float64)).sum())
+    rhs = float((g.astype(np.float64) * w.astype(np.float64)).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+    assert d8.get_status() == "OK"
