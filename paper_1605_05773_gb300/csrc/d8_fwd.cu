@@ -520,6 +520,7 @@ static cudaError_t launch_up_t(const DemTable& dt, const Pipe& p, int rule, cuda
 
 cudaError_t launch_up(const DemTable& dt, const Pipe& p, int mode, int rule, cudaStream_t s, int* nlaunch) {
   ++*nlaunch;
+  if (mode == UP_UNIT_Z || mode == UP_UNIT_DIR) return launch_up_unit(dt, p, mode == UP_UNIT_Z, rule, s);
 #define D8_UP_CASE(TT)                                                                      \
   case TT:                                                                                  \
     if (mode == UP_UNIT_Z) return launch_up_t<TT, uint32_t, UP_UNIT_Z>(dt, p, rule, s);     \
@@ -574,6 +575,7 @@ static cudaError_t launch_down_t(const DemTable& dt, const Pipe& p, cudaStream_t
 
 cudaError_t launch_down(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch) {
   ++*nlaunch;
+  if (!weighted) return launch_down_unit(dt, p, s);
   switch (p.T) {
     case 32: return weighted ? launch_down_t<32, ff>(dt, p, s) : launch_down_t<32, uint32_t>(dt, p, s);
     case 64: return weighted ? launch_down_t<64, ff>(dt, p, s) : launch_down_t<64, uint32_t>(dt, p, s);

@@ -65,6 +65,10 @@ cudaError_t launch_bwd_up(const DemTable& dt, const Pipe& p, cudaStream_t s, int
 cudaError_t launch_combine_bwd(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 
+// unit-count tile passes (d8_unit.cu)
+cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool from_z, int rule, cudaStream_t s);
+cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, cudaStream_t s);
+
 // shared-memory bytes of the per-tile kernels (0 = configuration unsupported)
 size_t up_smem_bytes(int T, int mode);
 size_t down_smem_bytes(int T, bool weighted);
