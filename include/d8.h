@@ -42,7 +42,8 @@ typedef enum {
   D8_ERR_CYCLE = 4,     /* device: the direction field contains a cycle */
   D8_ERR_NOMEM = 5,     /* workspace allocation failed */
   D8_ERR_CUDA = 6,      /* a CUDA runtime call failed */
-  D8_ERR_TIMEOUT = 7    /* device: a bounded wait gave up */
+  D8_ERR_TIMEOUT = 7,   /* device: a bounded wait gave up */
+  D8_ERR_CAPACITY = 8   /* grid larger than the fixed scratch of d8_flowdir_accumulate_noalloc */
 } d8_status;
 
 /* Direction rules ("The Algorithm": steepest slope, slope = drop divided by
@@ -146,6 +147,41 @@ const char* d8_stage_name(int stage);
 
 /* Library version string. */
 const char* d8_version(void);
+
+/* Directions and unit counts exactly as d8_flowdir_accumulate computes them,
+ * for callers that cannot allocate device memory when they call: processes
+ * running under a fixed memory budget reserved at start-up, callers whose
+ * pool or arena allocator owns all device memory, and callers that cannot
+ * create a context (d8_create allocates its status word and, later, its
+ * workspace).  This call needs no context and allocates nothing: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  The paper has no counterpart;
+ * this is an interface for such callers, not a step of the method.
+ *
+ * Its scratch is one fixed 64 MiB array inside the library, held by every GPU
+ * that loads the library until the process exits.  It fits grids of up to
+ * about 11,900 tiles of 64 x 64 cells (ceil(H/64) * ceil(W/64) tiles, e.g.
+ * 6976 x 6976, ~48 M cells); larger grids return D8_ERR_CAPACITY before any
+ * GPU work is queued.  Tile side 64, whatever d8_set_tile says elsewhere.
+ *
+ * z, dir, A: as d8_flowdir_accumulate (device pointers on the current device,
+ * owned by the caller).  status: optional device pointer to one uint32 that
+ * the call first clears and then ORs device-side errors into as
+ * (1 << d8_status) bits (non-finite z, invalid code, cycle); NULL discards
+ * them.  Asynchronous on `stream`.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before capturing any stream into a CUDA graph.  All calls share the one
+ * scratch array and it keeps the previous call's contents (the call clears
+ * what must start at zero itself); calls whose GPU work can overlap in time --
+ * on different streams or from different threads without ordering between
+ * them -- race on it and give wrong results.
+ *
+ * Errors: D8_ERR_ARG, D8_ERR_SHAPE (H*W > 2^32 - 1), D8_ERR_CAPACITY,
+ * D8_ERR_CUDA. */
+d8_status d8_flowdir_accumulate_noalloc(const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
+                                        uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA, uint32_t* status,
+                                        d8_stream stream);
 
 #ifdef __cplusplus
 }

@@ -230,6 +230,7 @@ const char* d8_status_string(d8_status s) {
     case D8_ERR_NOMEM: return "out of device memory";
     case D8_ERR_CUDA: return "CUDA runtime error";
     case D8_ERR_TIMEOUT: return "bounded device wait timed out";
+    case D8_ERR_CAPACITY: return "grid exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }
