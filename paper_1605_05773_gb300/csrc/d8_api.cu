@@ -64,6 +64,16 @@ struct d8_batch {
   int graph_rule = -1;
   cudaStream_t graph_stream = nullptr;
   int launches_per_run = 0;
+  // layered combine: per level l >= 1, a table of per-DEM unit grids and a
+  // unit -> DEM map (level 0 uses the tile table above)
+  int nlev = 0;
+  bool need_top = false;
+  int lev_S[HMAX + 1] = {};
+  int64_t lev_units[HMAX + 1] = {};
+  std::vector<DemDesc> lev_host[HMAX + 1];
+  DemDesc* lev_desc[HMAX + 1] = {};
+  int32_t* lev_map[HMAX + 1] = {};
+  size_t pipe_part = 0;
 };
 
 namespace {
@@ -144,6 +154,90 @@ Pipe carve_pipe(void* base, int64_t ntiles, int T, size_t vbytes, uint32_t* stat
   return p;
 }
 
+// ---- layered combine plan (single DEM or batch) ---------------------------
+struct HShape {
+  int nlev = 0;
+  int S[HMAX + 1] = {};
+  int64_t nunits[HMAX + 1] = {};
+  bool need_top = false;
+};
+
+// Levels above tiles of side T for the given DEM shapes.
+HShape hier_shape(int T, int n, const int64_t* H, const int64_t* W) {
+  HShape hs;
+  int64_t mx = 1;
+  for (int k = 0; k < n; k++) mx = H[k] > mx ? H[k] : (W[k] > mx ? W[k] : mx);
+  for (int k = 0; k < n; k++) mx = W[k] > mx ? W[k] : mx;
+  int S[HMAX], G[HMAX];
+  hs.nlev = hier_levels(T, mx, S, G, HMAX - 1);
+  hs.S[0] = T;
+  for (int l = 1; l <= hs.nlev; l++) hs.S[l] = S[l - 1] * G[l - 1];
+  for (int l = 0; l <= hs.nlev; l++) {
+    int64_t u = 0;
+    for (int k = 0; k < n; k++) {
+      const int64_t nu = ((H[k] + hs.S[l] - 1) / hs.S[l]) * ((W[k] + hs.S[l] - 1) / hs.S[l]);
+      u += nu;
+      if (l == hs.nlev && nu > 1) hs.need_top = true;
+    }
+    hs.nunits[l] = u;
+  }
+  return hs;
+}
+
+size_t hier_bytes(const HShape& hs) {
+  size_t b = 0;
+  for (int l = 1; l <= hs.nlev; l++) {
+    const size_t ns = (size_t)hs.nunits[l] * 4 * hs.S[l];
+    b += align256(ns * 2) + 2 * align256(ns * 4);
+  }
+  const size_t nt = (size_t)hs.nunits[hs.nlev] * 4 * hs.S[hs.nlev];
+  if (hs.need_top) b += 3 * align256(nt * 4);
+  b += align256(sizeof(uint32_t) * 64);
+  return b;
+}
+
+// Carve the level arrays; level 0 takes the tile pipeline's arrays.  `dts`
+// holds each level's DEM table (filled by the caller).
+HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dts) {
+  HPlan hp{};
+  hp.nlev = hs.nlev;
+  hp.need_top = hs.need_top;
+  hp.status = p.status;
+  hp.lev[0].S = hs.S[0];
+  hp.lev[0].nunits = hs.nunits[0];
+  hp.lev[0].dt = dts[0];
+  hp.lev[0].pex = p.pex;
+  hp.lev[0].pval = static_cast<uint32_t*>(p.pval);
+  hp.lev[0].fin = static_cast<uint32_t*>(p.S);
+  char* q = static_cast<char*>(base);
+  for (int l = 1; l <= hs.nlev; l++) {
+    const size_t ns = (size_t)hs.nunits[l] * 4 * hs.S[l];
+    HLevel& L = hp.lev[l];
+    L.S = hs.S[l];
+    L.nunits = hs.nunits[l];
+    L.dt = dts[l];
+    L.pex = reinterpret_cast<uint16_t*>(q);
+    q += align256(ns * 2);
+    L.pval = reinterpret_cast<uint32_t*>(q);
+    q += align256(ns * 4);
+    L.fin = reinterpret_cast<uint32_t*>(q);
+    q += align256(ns * 4);
+  }
+  const size_t nt = (size_t)hs.nunits[hs.nlev] * 4 * hs.S[hs.nlev];
+  if (hs.need_top) {
+    hp.top.par = reinterpret_cast<uint32_t*>(q);
+    q += align256(nt * 4);
+    hp.top.deg = reinterpret_cast<uint32_t*>(q);
+    q += align256(nt * 4);
+    hp.top.list = reinterpret_cast<uint32_t*>(q);
+    q += align256(nt * 4);
+  }
+  hp.queue = reinterpret_cast<uint32_t*>(q);
+  hp.top.counters = hp.queue + 48;
+  hp.top.status = p.status;
+  return hp;
+}
+
 d8_status ensure_ws(d8_ctx* c, size_t bytes) {
   if (c->ws_bytes >= bytes) return D8_OK;
   if (c->ws) {
@@ -191,7 +285,14 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   const bool weighted = (mode == UP_WEIGHTED);
   const size_t vb = weighted ? 8 : 4;
   if (up_smem_bytes(T, mode) == 0 || down_smem_bytes(T, weighted) == 0) return D8_ERR_ARG;
-  d8_status st = ensure_ws(c, pipe_bytes(ntiles, T, vb));
+  HShape hs;
+  size_t hb = 0;
+  if (!weighted) {
+    hs = hier_shape(T, 1, &d.H, &d.W);
+    hb = hier_bytes(hs);
+  }
+  const size_t pb = align256(pipe_bytes(ntiles, T, vb));
+  d8_status st = ensure_ws(c, pb + hb);
   if (st != D8_OK) return st;
   Pipe p = carve_pipe(c->ws, ntiles, T, vb, c->status);
   DemTable dt = single(d);
@@ -204,7 +305,20 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   if (e != cudaSuccess) return cuda_fail(e);
   {
     StageScope sc(c, ST_COMBINE, s);
-    e = launch_combine_fwd(dt, p, weighted, s, &sc.n);
+    if (weighted) {
+      e = launch_combine_fwd(dt, p, weighted, s, &sc.n);
+    } else {
+      DemTable dts[HMAX + 1];
+      for (int l = 0; l <= hs.nlev; l++) {
+        DemDesc dl = d;
+        dl.ntx = (d.W + hs.S[l] - 1) / hs.S[l];
+        dl.nty = (d.H + hs.S[l] - 1) / hs.S[l];
+        dl.tile_base = 0;
+        dts[l] = single(dl);
+      }
+      const HPlan hp = carve_hier(static_cast<char*>(c->ws) + pb, hs, p, dts);
+      e = launch_combine_hier(hp, s, &sc.n);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e);
   {
@@ -460,7 +574,36 @@ d8_status d8_batch_plan(d8_ctx* c, int n, const int64_t* H, const int64_t* W, d8
     const DemDesc& d = b->host_desc[k];
     for (int64_t t = 0; t < d.ntx * d.nty; t++) tile_dem[(size_t)(d.tile_base + t)] = k;
   }
-  b->ws_bytes = pipe_bytes(base, b->T, 4);
+  std::vector<int64_t> Hv(H, H + n), Wv(W, W + n);
+  const HShape hs = hier_shape(b->T, n, Hv.data(), Wv.data());
+  b->nlev = hs.nlev;
+  b->need_top = hs.need_top;
+  for (int l = 0; l <= hs.nlev; l++) {
+    b->lev_S[l] = hs.S[l];
+    b->lev_units[l] = hs.nunits[l];
+  }
+  b->pipe_part = align256(pipe_bytes(base, b->T, 4));
+  b->ws_bytes = b->pipe_part + hier_bytes(hs);
+  for (int l = 1; l <= hs.nlev; l++) {
+    std::vector<int32_t> map((size_t)hs.nunits[l]);
+    b->lev_host[l].resize(n);
+    int64_t ub = 0;
+    for (int k = 0; k < n; k++) {
+      DemDesc d = make_desc(H[k], W[k], hs.S[l]);
+      d.ldz = d.lddir = d.ldA = W[k];
+      d.tile_base = ub;
+      for (int64_t u = 0; u < d.ntx * d.nty; u++) map[(size_t)(ub + u)] = k;
+      ub += d.ntx * d.nty;
+      b->lev_host[l][k] = d;
+    }
+    if (cudaMalloc(&b->lev_desc[l], sizeof(DemDesc) * n) != cudaSuccess ||
+        cudaMalloc(&b->lev_map[l], sizeof(int32_t) * map.size()) != cudaSuccess ||
+        cudaMemcpy(b->lev_map[l], map.data(), sizeof(int32_t) * map.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      d8_batch_destroy(b);
+      return D8_ERR_NOMEM;
+    }
+  }
   if (cudaMalloc(&b->dev_desc, sizeof(DemDesc) * n) != cudaSuccess ||
       cudaMalloc(&b->dev_tile_dem, sizeof(int32_t) * (size_t)base) != cudaSuccess ||
       cudaMalloc(&b->ws, b->ws_bytes) != cudaSuccess) {
@@ -485,9 +628,27 @@ static cudaError_t batch_enqueue(d8_batch* b, int rule, cudaStream_t s, int* n_u
   dt.one = b->host_desc[0];
   if (b->n == 1) dt.ndem = 1;
   Pipe p = carve_pipe(b->ws, b->ntiles, b->T, 4, b->ctx->status);
+  HShape hs;
+  hs.nlev = b->nlev;
+  hs.need_top = b->need_top;
+  DemTable dts[HMAX + 1];
+  dts[0] = dt;
+  for (int l = 0; l <= b->nlev; l++) {
+    hs.S[l] = b->lev_S[l];
+    hs.nunits[l] = b->lev_units[l];
+    if (l == 0) continue;
+    DemTable t{};
+    t.ndem = b->n;
+    t.one = b->lev_host[l][0];
+    t.table = b->lev_desc[l];
+    t.tile_dem = b->lev_map[l];
+    if (b->n == 1) t.ndem = 1;
+    dts[l] = t;
+  }
+  const HPlan hp = carve_hier(static_cast<char*>(b->ws) + b->pipe_part, hs, p, dts);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
   if (e == cudaSuccess) e = launch_up(dt, p, UP_UNIT_Z, rule, s, n_up);
-  if (e == cudaSuccess) e = launch_combine_fwd(dt, p, false, s, n_comb);
+  if (e == cudaSuccess) e = launch_combine_hier(hp, s, n_comb);
   if (e == cudaSuccess) e = launch_down(dt, p, false, s, n_down);
   return e;
 }
@@ -507,6 +668,14 @@ d8_status d8_batch_flowdir_accumulate(d8_batch* b, const float* const* z, uint8_
   // the descriptor table is read by the kernels at run time, so new buffer
   // pointers need no re-capture: upload it ahead of the graph on the stream
   cudaError_t e = cudaMemcpyAsync(b->dev_desc, b->host_desc.data(), sizeof(DemDesc) * b->n, cudaMemcpyHostToDevice, s);
+  for (int l = 1; l <= b->nlev && e == cudaSuccess; l++) {
+    for (int k = 0; k < b->n; k++) {
+      b->lev_host[l][k].z = z[k];
+      b->lev_host[l][k].dir = dir[k];
+      b->lev_host[l][k].A = A[k];
+    }
+    e = cudaMemcpyAsync(b->lev_desc[l], b->lev_host[l].data(), sizeof(DemDesc) * b->n, cudaMemcpyHostToDevice, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   if (b->n == 1 || !b->exec || b->graph_rule != (int)rule) {
     if (b->exec) {
@@ -561,6 +730,10 @@ d8_status d8_batch_destroy(d8_batch* b) {
   if (b->dev_desc) cudaFree(b->dev_desc);
   if (b->dev_tile_dem) cudaFree(b->dev_tile_dem);
   if (b->ws) cudaFree(b->ws);
+  for (int l = 0; l <= HMAX; l++) {
+    if (b->lev_desc[l]) cudaFree(b->lev_desc[l]);
+    if (b->lev_map[l]) cudaFree(b->lev_map[l]);
+  }
   delete b;
   return D8_OK;
 }

@@ -1,0 +1,505 @@
+// d8_combine.cu -- the combine of the unit-count pipeline (Algorithms 5-6),
+// layered as the paper's conclusion suggests.
+//
+// Level 0 units are the tiles; each has a perimeter summary (per perimeter
+// slot: the exit of the slot's in-tile path, and the in-tile count at exits).
+// A level-l unit ("group") is a G x G block of level-(l-1) units.  The exits
+// of the children form a forest inside the group: a child exit's parent is
+// the child exit that its successor's path reaches next.  k_group_up solves
+// that forest in shared memory with the same last-arriver walks as the tiles
+// (Algorithm 2 on the exit forest) and writes the group's own perimeter
+// summary in the same format -- so the next level runs the same kernel.
+// Above the last shared-memory level, k_top_* solve the remaining exit forest
+// in global memory: the master's queue method (Algorithms 5-6) with global
+// atomics, a short walk because few units remain.  k_group_down then runs
+// each level back down: the resolved inflow across a group's border seeds
+// its child exits and the same walks give every child exit its final area;
+// at level 0 that is the final area of every tile exit, which the tiles'
+// finalising pass reads.
+#include "d8_device.cuh"
+
+namespace d8 {
+
+namespace cmb {
+
+constexpr int NTG = 256;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr uint16_t N_ROOT = 0xFFFFu;  // path ends inside the group
+constexpr uint16_t N_OUT = 0xFFFEu;   // parent lies outside the group (a group exit)
+constexpr uint16_t N_NONE = 0xFFFDu;  // not an exit slot
+
+template <int S, int G>
+struct GroupLayout {
+  static constexpr int NS = G * G * 4 * S;  // child slots of a group
+  static constexpr size_t off_spx = 0;                      // u16 child exit codes
+  static constexpr size_t off_par = off_spx + (size_t)NS * 2;  // u16 parent node
+  static constexpr size_t off_val = off_par + (size_t)NS * 2;  // u32 value
+  static constexpr size_t off_deg = off_val + (size_t)NS * 4;  // u32 unfinished children
+  static constexpr size_t off_src = off_deg + (size_t)NS * 4;  // u16 source lists
+  static constexpr size_t off_misc = off_src + (size_t)NS * 2;
+  static constexpr size_t bytes = off_misc + 64;
+};
+
+__device__ __forceinline__ DemDesc dem_by_index(const DemTable& t, int k) { return t.ndem == 1 ? t.one : t.table[k]; }
+
+struct UnitGeo {
+  int64_t i0, j0;
+  int h, w;
+};
+
+__device__ __forceinline__ UnitGeo unit_geo(const DemDesc& d, int64_t uy, int64_t ux, int S) {
+  UnitGeo u;
+  u.i0 = uy * S;
+  u.j0 = ux * S;
+  u.h = (int)min64(S, d.H - u.i0);
+  u.w = (int)min64(S, d.W - u.j0);
+  return u;
+}
+
+// Load the children of group (gy, gx) and compute every child exit's parent
+// inside the group and the children count of every node.
+// Returns the number of child exits this thread loaded.
+template <int S, int G>
+__device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint16_t* cpex, const uint32_t* cpval,
+                          uint16_t* spx, uint16_t* par, uint32_t* val, uint32_t* deg) {
+  constexpr int NS = G * G * 4 * S;
+  int exits = 0;
+  for (int n = threadIdx.x; n < NS; n += NTG) {
+    const int lt = n / (4 * S), s = n - lt * (4 * S);
+    const int64_t cy = gy * G + lt / G, cx = gx * G + lt % G;
+    uint16_t pe = PEX_TERM;
+    uint32_t v = 0;
+    if (cy < cd.nty && cx < cd.ntx) {
+      const int64_t cu = cd.tile_base + cy * cd.ntx + cx;
+      pe = cpex[cu * (4 * S) + s];
+      if (pe & PEX_EXIT) {
+        v = cpval[cu * (4 * S) + s];
+        exits++;
+      }
+    }
+    spx[n] = pe;
+    val[n] = v;
+    deg[n] = 0;
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < NS; n += NTG) {
+    const uint16_t pe = spx[n];
+    uint16_t pr = N_NONE;
+    if (pe & PEX_EXIT) {
+      const int lt = n / (4 * S), s = n - lt * (4 * S);
+      const int64_t cy = gy * G + lt / G, cx = gx * G + lt % G;
+      const UnitGeo u = unit_geo(cd, cy, cx, S);
+      int i, j;
+      slot_cell(s, u.h, u.w, S, i, j);
+      const int k = pe & 7;
+      const int64_t ti = u.i0 + i + code_di(k), tj = u.j0 + j + code_dj(k);
+      const int64_t ty = ti / S, tx = tj / S;
+      const int64_t a = ty - gy * G, b = tx - gx * G;
+      if (a >= 0 && b >= 0 && a < G && b < G) {
+        const UnitGeo tu = unit_geo(cd, ty, tx, S);
+        const int lt2 = (int)(a * G + b);
+        const int n2 = lt2 * (4 * S) + slot_of((int)(ti - tu.i0), (int)(tj - tu.j0), tu.h, tu.w, S);
+        const uint16_t pe2 = spx[n2];
+        if (pe2 & PEX_EXIT)
+          pr = (uint16_t)n2;
+        else if (pe2 == PEX_TERM)
+          pr = N_ROOT;
+        else
+          pr = (uint16_t)(lt2 * (4 * S) + pe2);
+        if (pr < N_NONE) atomicAdd(&deg[pr], 1u);
+      } else {
+        pr = N_OUT;
+      }
+    }
+    par[n] = pr;
+  }
+  __syncthreads();
+  return exits;
+}
+
+// Algorithm 2 on the exit forest of a group: last-arriver walks from the
+// nodes without unfinished children.  A finished node adds its value to its
+// parent, then (after a block fence) decrements the parent's children count;
+// the last child continues at the parent (after a fence, so it sees every
+// child's addition).  Returns the number of nodes this thread finished.
+template <int S, int G>
+__device__ int group_walk(uint16_t* spx, const uint16_t* par, uint32_t* val, uint32_t* deg, uint16_t* srcl) {
+  constexpr int NS = G * G * 4 * S;
+  constexpr int NW = NTG / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint16_t* my = srcl + warp * (NS / NW);
+  int n = 0;
+  for (int r = 0; r < NS / NTG; r++) {
+    const int c = threadIdx.x + r * NTG;
+    const bool s = (spx[c] & PEX_EXIT) && deg[c] == 0u;
+    const unsigned m = __ballot_sync(FULL, s);
+    if (s) my[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)c;
+    n += __popc(m);
+  }
+  __syncthreads();
+  int done = 0, head = 0, cur = -1;
+  uint32_t v = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (;;) {
+    if (head < n) {
+      const unsigned need = __ballot_sync(FULL, cur < 0);
+      const int idx = head + __popc(need & lt);
+      if (cur < 0 && idx < n) {
+        cur = my[idx];
+        v = val[cur];
+        done++;
+      }
+      head += __popc(need);
+    } else if (!__any_sync(FULL, cur >= 0)) {
+      break;
+    }
+    if (cur >= 0) {
+      const uint16_t p = par[cur];
+      if (p >= N_NONE) {
+        cur = -1;
+        continue;
+      }
+      atomicAdd(&val[p], v);
+      __threadfence_block();
+      const uint32_t old = atomicSub(&deg[p], 1u);
+      if (old == 1u) {
+        __threadfence_block();
+        cur = p;
+        v = *(volatile uint32_t*)&val[p];
+        done++;
+      } else {
+        cur = -1;
+      }
+    }
+  }
+  return done;
+}
+
+template <int S, int G>
+__global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, const uint16_t* cpex,
+                                                    const uint32_t* cpval, uint16_t* gpex, uint32_t* gpval,
+                                                    int64_t ngroups, uint32_t* queue, uint32_t* status) {
+  using L = GroupLayout<S, G>;
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint16_t* spx = reinterpret_cast<uint16_t*>(sm + L::off_spx);
+  uint16_t* par = reinterpret_cast<uint16_t*>(sm + L::off_par);
+  uint32_t* val = reinterpret_cast<uint32_t*>(sm + L::off_val);
+  uint32_t* deg = reinterpret_cast<uint32_t*>(sm + L::off_deg);
+  uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
+  int* misc = reinterpret_cast<int*>(sm + L::off_misc);
+  constexpr int NS = L::NS;
+  constexpr int GS = G * S;
+  for (int64_t gu = next_tile(queue); gu < ngroups; gu = next_tile(queue)) {
+    const DemDesc gd = dem_of(gdt, gu);
+    const int dem = gdt.ndem == 1 ? 0 : gdt.tile_dem[gu];
+    const DemDesc cd = dem_by_index(cdt, dem);
+    const int64_t lg = gu - gd.tile_base;
+    const int64_t gy = lg / gd.ntx, gx = lg % gd.ntx;
+    if (threadIdx.x == 0) {
+      misc[0] = 0;
+      misc[1] = 0;
+    }
+    const int exits = group_load<S, G>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
+    const int done = group_walk<S, G>(spx, par, val, deg, srcl);
+    atomicAdd(&misc[0], done);
+    atomicAdd(&misc[1], exits);
+    __syncthreads();
+    // every exit node must have been finished, else the exit graph has a cycle
+    if (threadIdx.x == 0 && misc[0] != misc[1]) set_status(status, D8_ERR_CYCLE);
+    // the group's own perimeter summary
+    const UnitGeo gg = unit_geo(gd, gy, gx, GS);
+    for (int gs = threadIdx.x; gs < 4 * GS; gs += NTG) {
+      int ci, cj;
+      uint16_t gpe = PEX_TERM;
+      uint32_t gv = 0;
+      if (slot_cell(gs, gg.h, gg.w, GS, ci, cj)) {
+        const int a = ci / S, b = cj / S;
+        const UnitGeo cu = unit_geo(cd, gy * G + a, gx * G + b, S);
+        const int lt = a * G + b;
+        const int n0 = lt * (4 * S) + slot_of(ci - a * S, cj - b * S, cu.h, cu.w, S);
+        const uint16_t pe = spx[n0];
+        int x = -1;
+        if (pe & PEX_EXIT) {
+          if (par[n0] == N_OUT) {
+            gpe = (uint16_t)(PEX_EXIT | (pe & 7));
+            gv = val[n0];
+          } else {
+            x = n0;
+          }
+        } else if (pe != PEX_TERM) {
+          x = lt * (4 * S) + pe;
+        }
+        if (x >= 0) {
+          for (int it = 0; it < NS && par[x] < N_NONE; it++) x = par[x];
+          if (par[x] == N_OUT) {
+            const int xlt = x / (4 * S), xs = x - xlt * (4 * S);
+            const UnitGeo xu = unit_geo(cd, gy * G + xlt / G, gx * G + xlt % G, S);
+            int xi, xj;
+            slot_cell(xs, xu.h, xu.w, S, xi, xj);
+            gpe = (uint16_t)slot_of((xlt / G) * S + xi, (xlt % G) * S + xj, gg.h, gg.w, GS);
+          }
+        }
+      }
+      gpex[gu * (4 * GS) + gs] = gpe;
+      gpval[gu * (4 * GS) + gs] = gv;
+    }
+    // (next_tile's barrier protects shared memory before the next group)
+  }
+}
+
+template <int S, int G>
+__global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, const uint16_t* cpex,
+                                                      const uint32_t* cpval, uint32_t* cfin, const uint32_t* gfin,
+                                                      int64_t ngroups, uint32_t* queue) {
+  using L = GroupLayout<S, G>;
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint16_t* spx = reinterpret_cast<uint16_t*>(sm + L::off_spx);
+  uint16_t* par = reinterpret_cast<uint16_t*>(sm + L::off_par);
+  uint32_t* val = reinterpret_cast<uint32_t*>(sm + L::off_val);
+  uint32_t* deg = reinterpret_cast<uint32_t*>(sm + L::off_deg);
+  uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
+  constexpr int NS = L::NS;
+  constexpr int GS = G * S;
+  for (int64_t gu = next_tile(queue); gu < ngroups; gu = next_tile(queue)) {
+    const DemDesc gd = dem_of(gdt, gu);
+    const int dem = gdt.ndem == 1 ? 0 : gdt.tile_dem[gu];
+    const DemDesc cd = dem_by_index(cdt, dem);
+    const int64_t lg = gu - gd.tile_base;
+    const int64_t gy = lg / gd.ntx, gx = lg % gd.ntx;
+    group_load<S, G>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
+    // inflow across the group border: each border cell r receives the final
+    // areas of the outside cells draining into it; the inflow then follows
+    // r's path inside its child unit to that child's exit
+    const UnitGeo gg = unit_geo(gd, gy, gx, GS);
+    for (int gs = threadIdx.x; gs < 4 * GS; gs += NTG) {
+      int ci, cj;
+      if (!slot_cell(gs, gg.h, gg.w, GS, ci, cj)) continue;
+      const int64_t gi = gg.i0 + ci, gj = gg.j0 + cj;
+      uint32_t in = 0;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int li = ci + code_di(k), lj = cj + code_dj(k);
+        if (li >= 0 && lj >= 0 && li < gg.h && lj < gg.w) continue;
+        const int64_t ni = gi + code_di(k), nj = gj + code_dj(k);
+        if (ni < 0 || nj < 0 || ni >= gd.H || nj >= gd.W) continue;
+        if (gd.dir[ni * gd.lddir + nj] != opposite(k)) continue;
+        in += gfin[global_slot(gd, ni, nj, GS)];
+      }
+      if (!in) continue;
+      const int a = ci / S, b = cj / S;
+      const UnitGeo cu = unit_geo(cd, gy * G + a, gx * G + b, S);
+      const int lt = a * G + b;
+      const int n0 = lt * (4 * S) + slot_of(ci - a * S, cj - b * S, cu.h, cu.w, S);
+      const uint16_t pe = spx[n0];
+      if (pe & PEX_EXIT)
+        atomicAdd(&val[n0], in);
+      else if (pe != PEX_TERM)
+        atomicAdd(&val[lt * (4 * S) + pe], in);
+    }
+    __syncthreads();
+    group_walk<S, G>(spx, par, val, deg, srcl);
+    __syncthreads();
+    for (int n = threadIdx.x; n < NS; n += NTG) {
+      if (!(spx[n] & PEX_EXIT)) continue;
+      const int lt = n / (4 * S), s = n - lt * (4 * S);
+      const int64_t cy = gy * G + lt / G, cx = gx * G + lt % G;
+      cfin[(cd.tile_base + cy * cd.ntx + cx) * (4 * S) + s] = val[n];
+    }
+  }
+}
+
+// ---- top level: Algorithms 5-6 over the remaining units, in global memory
+
+template <int S>
+__global__ void k_top_init(DemTable dt, const uint16_t* pex, const uint32_t* pval, uint32_t* fin, uint32_t* par,
+                           uint32_t* deg, int64_t nslots) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
+    const uint16_t pe = pex[g];
+    uint32_t pr = ROOT;
+    if (pe & PEX_EXIT) {
+      const int64_t t = g / (4 * S);
+      const int s = (int)(g - t * (4 * S));
+      const DemDesc d = dem_of(dt, t);
+      const int64_t lt = t - d.tile_base;
+      const UnitGeo u = unit_geo(d, lt / d.ntx, lt % d.ntx, S);
+      int i, j;
+      slot_cell(s, u.h, u.w, S, i, j);
+      const int k = pe & 7;
+      const int64_t y = global_slot(d, u.i0 + i + code_di(k), u.j0 + j + code_dj(k), S);
+      const uint16_t pey = pex[y];
+      if (pey & PEX_EXIT)
+        pr = (uint32_t)y;
+      else if (pey != PEX_TERM)
+        pr = (uint32_t)((y / (4 * S)) * (4 * S) + pey);
+      if (pr != ROOT) atomicAdd(&deg[pr], 1u);
+      fin[g] = pval[g];
+    }
+    par[g] = pr;
+  }
+}
+
+__global__ void k_top_sources(const uint16_t* pex, const uint32_t* deg, uint32_t* list, uint32_t* counters,
+                              int64_t nslots) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
+    if ((pex[g] & PEX_EXIT) && deg[g] == 0u) list[atomicAdd(&counters[0], 1u)] = (uint32_t)g;
+    if (pex[g] & PEX_EXIT) atomicAdd(&counters[1], 1u);
+  }
+}
+
+// Algorithm 6 with global atomics: last-arriver walks up the exit forest.
+__global__ void k_top_walk(const uint32_t* par, uint32_t* fin, uint32_t* deg, const uint32_t* list,
+                           uint32_t* counters) {
+  const uint32_t n = *(volatile const uint32_t*)&counters[0];
+  uint32_t done = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t x = list[i];
+    uint32_t v = fin[x];
+    done++;
+    for (;;) {
+      const uint32_t p = par[x];
+      if (p == ROOT) break;
+      atomicAdd(&fin[p], v);
+      __threadfence();
+      if (atomicSub(&deg[p], 1u) != 1u) break;
+      __threadfence();
+      x = p;
+      v = *(volatile uint32_t*)&fin[p];
+      done++;
+    }
+  }
+  if (done) atomicAdd(&counters[2], done);
+}
+
+__global__ void k_top_check(const uint32_t* counters, uint32_t* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && counters[1] != counters[2]) set_status(status, D8_ERR_CYCLE);
+}
+
+template <int S, int G>
+static cudaError_t launch_level_up(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex,
+                                   const uint32_t* cpval, uint16_t* gpex, uint32_t* gpval, int64_t ngroups,
+                                   uint32_t* queue, uint32_t* status, cudaStream_t s) {
+  using L = GroupLayout<S, G>;
+  cudaError_t e = cudaFuncSetAttribute(k_group_up<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1, dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_up<S, G>, NTG, L::bytes);
+  int64_t grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * sms;
+  if (grid > ngroups) grid = ngroups;
+  e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  k_group_up<S, G><<<(unsigned)grid, NTG, L::bytes, s>>>(cdt, gdt, cpex, cpval, gpex, gpval, ngroups, queue, status);
+  return cudaGetLastError();
+}
+
+template <int S, int G>
+static cudaError_t launch_level_down(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex,
+                                     const uint32_t* cpval, uint32_t* cfin, const uint32_t* gfin, int64_t ngroups,
+                                     uint32_t* queue, cudaStream_t s) {
+  using L = GroupLayout<S, G>;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_group_down<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1, dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_down<S, G>, NTG, L::bytes);
+  int64_t grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * sms;
+  if (grid > ngroups) grid = ngroups;
+  e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  k_group_down<S, G><<<(unsigned)grid, NTG, L::bytes, s>>>(cdt, gdt, cpex, cpval, cfin, gfin, ngroups, queue);
+  return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& top, cudaStream_t s, int* nl) {
+  const int64_t ns = lv.nunits * 4 * S;
+  cudaError_t e = cudaMemsetAsync(top.deg, 0, sizeof(uint32_t) * (size_t)ns, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(top.counters, 0, sizeof(uint32_t) * 4, s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (ns + 255) / 256;
+  if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
+  if (b < 1) b = 1;
+  k_top_init<S><<<(unsigned)b, 256, 0, s>>>(dt, lv.pex, lv.pval, lv.fin, top.par, top.deg, ns);
+  k_top_sources<<<(unsigned)b, 256, 0, s>>>(lv.pex, top.deg, top.list, top.counters, ns);
+  k_top_walk<<<(unsigned)(sms * 8), 256, 0, s>>>(top.par, lv.fin, top.deg, top.list, top.counters);
+  k_top_check<<<1, 32, 0, s>>>(top.counters, top.status);
+  *nl += 4;
+  return cudaGetLastError();
+}
+
+}  // namespace cmb
+
+// Level schedule: tiles of side T, then groups of G = 4 (from 32 or 64) or
+// G = 2 children, up to a group side of 1024 cells.
+int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels) {
+  int n = 0;
+  int s = T;
+  while (n < max_levels && s < max_side && s < 1024) {
+    const int g = (s <= 64) ? 4 : 2;
+    S[n] = s;
+    G[n] = g;
+    s *= g;
+    n++;
+  }
+  return n;
+}
+
+cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch) {
+  cudaError_t e = cudaSuccess;
+  // up: level l-1 -> l
+  for (int l = 1; l <= hp.nlev && e == cudaSuccess; l++) {
+    const HLevel& c = hp.lev[l - 1];
+    const HLevel& g = hp.lev[l];
+    const int S = c.S, G = g.S / c.S;
+#define D8_UP(SS, GG)                                                                                            \
+  if (S == SS && G == GG) {                                                                                     \
+    e = cmb::launch_level_up<SS, GG>(c.dt, g.dt, c.pex, c.pval, g.pex, g.pval, g.nunits, hp.queue + l, hp.status, s); \
+    ++*nlaunch;                                                                                                 \
+    continue;                                                                                                   \
+  }
+    D8_UP(32, 4) D8_UP(64, 4) D8_UP(128, 2) D8_UP(256, 2) D8_UP(512, 2)
+#undef D8_UP
+    return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  // top
+  const HLevel& t = hp.lev[hp.nlev];
+  if (hp.need_top) {
+    switch (t.S) {
+      case 32: e = cmb::launch_top<32>(t.dt, t, hp.top, s, nlaunch); break;
+      case 64: e = cmb::launch_top<64>(t.dt, t, hp.top, s, nlaunch); break;
+      case 128: e = cmb::launch_top<128>(t.dt, t, hp.top, s, nlaunch); break;
+      case 256: e = cmb::launch_top<256>(t.dt, t, hp.top, s, nlaunch); break;
+      case 512: e = cmb::launch_top<512>(t.dt, t, hp.top, s, nlaunch); break;
+      case 1024: e = cmb::launch_top<1024>(t.dt, t, hp.top, s, nlaunch); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  // down: level l -> l-1
+  for (int l = hp.nlev; l >= 1 && e == cudaSuccess; l--) {
+    const HLevel& c = hp.lev[l - 1];
+    const HLevel& g = hp.lev[l];
+    const int S = c.S, G = g.S / c.S;
+#define D8_DN(SS, GG)                                                                                                \
+  if (S == SS && G == GG) {                                                                                         \
+    e = cmb::launch_level_down<SS, GG>(c.dt, g.dt, c.pex, c.pval, c.fin, g.fin, g.nunits, hp.queue + 16 + l, s); \
+    ++*nlaunch;                                                                                                     \
+    continue;                                                                                                       \
+  }
+    D8_DN(32, 4) D8_DN(64, 4) D8_DN(128, 2) D8_DN(256, 2) D8_DN(512, 2)
+#undef D8_DN
+    return cudaErrorInvalidValue;
+  }
+  return e;
+}
+
+}  // namespace d8

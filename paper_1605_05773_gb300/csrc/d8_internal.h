@@ -65,6 +65,39 @@ cudaError_t launch_bwd_up(const DemTable& dt, const Pipe& p, cudaStream_t s, int
 cudaError_t launch_combine_bwd(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 
+// ---- layered combine (d8_combine.cu) --------------------------------------
+// Level 0 units are the tiles; a level-l unit is a G x G block of level-(l-1)
+// units.  Every level has per-unit perimeter summaries of the same format:
+// per perimeter slot the exit code (pex), the in-unit value at exits (pval)
+// and, after the down sweep, the final value at exits (fin).
+constexpr int HMAX = 8;
+struct HLevel {
+  int S;            // unit side in cells
+  int64_t nunits;   // units over all DEMs
+  DemTable dt;      // per-DEM unit grid (ntx, nty, tile_base) at this level
+  uint16_t* pex;
+  uint32_t* pval;
+  uint32_t* fin;
+};
+struct HTop {  // the top level's queue-method solve in global memory
+  uint32_t* par;
+  uint32_t* deg;
+  uint32_t* list;
+  uint32_t* counters;  // [0] sources, [1] exits, [2] finished
+  uint32_t* status;
+};
+struct HPlan {
+  int nlev;  // group levels 1..nlev above the tiles
+  HLevel lev[HMAX];
+  bool need_top;
+  HTop top;
+  uint32_t* queue;  // 32 work-queue counters
+  uint32_t* status;
+};
+// group sides of the levels above tiles of side T, for grids up to max_side
+int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels);
+cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch);
+
 // unit-count tile passes (d8_unit.cu)
 cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool from_z, int rule, cudaStream_t s);
 cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, cudaStream_t s);
