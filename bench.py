@@ -40,6 +40,26 @@ ALG_BYTES = {"tile_up": 5.0, "tile_down": 5.0, "flowdir": 5.0}  # per cell: z in
 PIPE_BYTES = 9.0  # z in (4) + dir out (1) + A out (4) per cell for the whole path
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per cell of a tile kernel from the committed ncu summary, or
+    None when the kernel source changed since that capture."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", "tile_kernels_fractal_8192.md")
+    src = os.path.join(ROOT, "paper_1605_05773_gb300", "csrc", "d8_unit.cu")
+    try:
+        text = open(prof).read().split()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+    if "kernel_source_sha1" not in text or text[text.index("kernel_source_sha1") + 1] != sha:
+        return None
+    for k in range(len(text) - 2):
+        if text[k] == "scaled_traffic_bytes_per_cell" and text[k + 1] == kernel:
+            return float(text[k + 2])
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -223,6 +243,7 @@ def run_ours(args, world, rank, local):
     dom = max((s for s in stages if stages[s][1] > 0 and s in ALG_BYTES), key=lambda s: stages[s][0])
     dom_ms = stages[dom][0] / args.steps
     achieved = ALG_BYTES[dom] * cells / (dom_ms / 1e3) / 1e9
+    tb = measured_traffic(dom)
     launches = sum(v[1] for v in stages.values())
 
     # end to end through the public API: pinned host z in, dirs + counts out
@@ -264,7 +285,9 @@ def run_ours(args, world, rank, local):
             "config": {"workload": args.workload, "description": desc, "H": H, "W": W, "tile": args.tile,
                        "l2": "inputs larger than L2 (4.3 GB z per step, 129 MB L2)", "parity_guard": ok},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": (tb * cells if tb else None),
+                         "traffic_note": "ncu dram bytes per cell at 8192^2 (profiles/tile_kernels_fractal_8192.md) x cells",
+                         "peak_kind": peak_kind,
                          "alg_bytes_per_cell": ALG_BYTES[dom], "ms_per_launch": dom_ms},
             "pipeline_roofline": {"alg_bytes_per_cell": PIPE_BYTES,
                                   "achieved": PIPE_BYTES * cells / (ms_max / args.steps / 1e3) / 1e9,
