@@ -4,9 +4,9 @@
 //               the in-tile dependency count (Algorithm 1), the in-tile
 //               up-slope counts with inflow from other tiles unknown = 0
 //               (Algorithms 2-4) and the perimeter summary.
-//  k_down_unit  per tile finalise (Algorithms 7-8): the resolved inflow from
-//               neighbouring tiles seeds the perimeter, the in-tile
-//               accumulation is re-run and the final counts are written.
+//  k_fin_unit   per tile finalise (Algorithms 7-8): A already holds the
+//               in-tile counts; the resolved inflow from neighbouring tiles
+//               is pushed down the in-tile paths it reaches and added there.
 //
 // Layout choices for GB300:
 //  * one packed 32-bit word per cell in shared memory holds the cell's
@@ -15,11 +15,10 @@
 //    to its down-slope cell and tells the sender whether it was the last
 //    input; only then does the sender continue (Algorithm 2's tail
 //    recursion).  The in-tile count of a 128 x 128 tile fits in 16 bits;
-//  * the finalising pass keeps the same 32-bit word and carries the resolved
-//    inflow (up to 2^32 - 1) in a side array; a per-word counter of inflow
-//    carriers tells the last arriver whether it must look there, and a
-//    block-scope fence pair orders the side-array update before the count
-//    update that publishes it;
+//  * the first pass writes the in-tile counts to A, so the finalising pass
+//    only walks the paths down-slope of the perimeter cells that receive
+//    inflow from other tiles, adding that inflow along them, instead of
+//    re-running the whole tile;
 //  * one warp spans the tile width, each lane owning T/32 adjacent columns:
 //    it slides a 3-row register window down its columns with vector loads of
 //    z straight from global memory (coalesced), left/right neighbours come
@@ -48,13 +47,11 @@ constexpr int NWALK = D8_WALK_WARPS;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // word: count 0..15 | inputs left 16..19 | code 20..23 | IN 24 | EXIT 25 |
-// PRESENT 26 | inflow carriers 27..31 (pass 2)
+// PRESENT 26
 constexpr uint32_t W_IN = 1u << 24, W_EXIT = 1u << 25, W_PRES = 1u << 26;
-constexpr uint32_t W_INF1 = 1u << 27;
 __device__ __forceinline__ uint32_t w_cnt(uint32_t w) { return w & 0xFFFFu; }
 __device__ __forceinline__ uint32_t w_left(uint32_t w) { return (w >> 16) & 0xFu; }
 __device__ __forceinline__ int w_code(uint32_t w) { return (int)((w >> 20) & 0xFu); }
-__device__ __forceinline__ uint32_t w_inf(uint32_t w) { return w >> 27; }
 
 // Segment records (one uint16 per cell).  A finished non-source cell holds
 // the source cell whose walk finished it.  A source cell holds its walk's end
@@ -63,15 +60,17 @@ __device__ __forceinline__ uint32_t w_inf(uint32_t w) { return w >> 27; }
 // walk stopped before that junction cell, which another walk finished).
 constexpr uint16_t SEG_REC = 0x8000u, SEG_END = 0x4000u;
 
-// in-tile offset of direction k (N, NE, E, SE, S, SW, W, NW) for row stride T
-__constant__ int c_toff32[8] = {-32, -31, 1, 33, 32, 31, -1, -33};
-__constant__ int c_toff64[8] = {-64, -63, 1, 65, 64, 63, -1, -65};
-__constant__ int c_toff128[8] = {-128, -127, 1, 129, 128, 127, -1, -129};
+// In-tile offset of direction k (N, NE, E, SE, S, SW, W, NW) for row stride T.
+// For T <= 64 the eight offsets fit in signed bytes of one 64-bit constant
+// held in registers (a __constant__ table indexed by each lane's own code
+// would be serialised across the distinct addresses of a warp).
 template <int T>
 __device__ __forceinline__ int toff_tab(int k) {
-  if (T == 32) return c_toff32[k];
-  if (T == 64) return c_toff64[k];
-  return c_toff128[k];
+  if (T == 64) return (int)(signed char)(0xBFFF3F404101C1C0ull >> (8 * k));
+  if (T == 32) return (int)(signed char)(0xDFFF1F202101E1E0ull >> (8 * k));
+  const int di = (int)((0x01222100u >> (4 * k)) & 0xFu) - 1;
+  const int dj = (int)((0x00012221u >> (4 * k)) & 0xFu) - 1;
+  return di * T + dj;
 }
 
 // D8 code of an interior cell from its 3x3 window (a = row above, b = own
@@ -157,12 +156,13 @@ struct UpLayout {
 };
 
 template <int T>
-struct DownLayout {
+struct FinLayout {
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t off_word = 0;
-  static constexpr size_t off_inf = TT * 4;
-  static constexpr size_t off_src = off_inf + TT * 4;
-  static constexpr size_t off_misc = off_src + TT * 2;
+  static constexpr size_t off_f = 0;                     // uint32 F per cell
+  static constexpr size_t off_code = TT * 4;             // uint8 code per cell
+  static constexpr size_t off_rcell = off_code + TT;     // uint16 per perimeter slot
+  static constexpr size_t off_rin = off_rcell + (size_t)4 * T * 2;  // uint32 per slot
+  static constexpr size_t off_misc = off_rin + (size_t)4 * T * 4;
   static constexpr size_t bytes = off_misc + 64;
 };
 
@@ -196,47 +196,61 @@ __device__ __forceinline__ void tile_dirs_from_z(const DemDesc& d, const TileGeo
     const int64_t gj = gjb + k;
     coledge[k] = (gj == 0) || (gj == d.W - 1);
   }
-  const float* p = d.z + (g.i0 + r0 - 1) * d.ldz + gjb;
+  const float* p0 = d.z + (g.i0 + r0 - 1) * d.ldz + gjb;
   uint8_t* dp = d.dir + (g.i0 + r0) * d.lddir + gjb;
-  float A[CPL + 2], B[CPL + 2], C[CPL + 2];
 
-  auto load = [&](float(&R)[CPL + 2], int li) {
+  // Raw values of one z row for this lane: own columns, plus the column to
+  // the left (lane 0) or right (lane holding the tile's last column).
+  struct Raw {
+    float v[CPL];
+    float l, r;
+  };
+  constexpr int NR = ROWS + 2;  // rows r0-1 .. r0+ROWS
+  constexpr int PD = 4;         // rows loaded ahead of use
+  auto issue = [&](Raw& R, int q) {
+    const int li = r0 - 1 + q;
     const bool rv = (li >= i_first) && (li < i_last) && ncols > 0;
+    const float* p = p0 + (int64_t)q * d.ldz;
     if (vec_ok) {
       if (CPL == 4) {
-        const float4 q = rv ? __ldg(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        R[1] = q.x;
-        R[2] = q.y;
-        R[CPL > 2 ? 3 : 1] = q.z;
-        R[CPL > 3 ? 4 : 1] = q.w;
+        const float4 t = rv ? __ldg(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        R.v[0] = t.x;
+        R.v[CPL > 1 ? 1 : 0] = t.y;
+        R.v[CPL > 2 ? 2 : 0] = t.z;
+        R.v[CPL > 3 ? 3 : 0] = t.w;
       } else if (CPL == 2) {
-        const float2 q = rv ? __ldg(reinterpret_cast<const float2*>(p)) : make_float2(0.f, 0.f);
-        R[1] = q.x;
-        R[CPL > 1 ? 2 : 1] = q.y;
+        const float2 t = rv ? __ldg(reinterpret_cast<const float2*>(p)) : make_float2(0.f, 0.f);
+        R.v[0] = t.x;
+        R.v[CPL > 1 ? 1 : 0] = t.y;
       } else {
-        R[1] = rv ? __ldg(p) : 0.0f;
+        R.v[0] = rv ? __ldg(p) : 0.0f;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < CPL; k++) R[1 + k] = (rv && k < ncols) ? __ldg(p + k) : 0.0f;
+      for (int k = 0; k < CPL; k++) R.v[k] = (rv && k < ncols) ? __ldg(p + k) : 0.0f;
     }
-    float ls = __shfl_up_sync(FULL, R[CPL], 1);
-    const float rs = __shfl_down_sync(FULL, R[1], 1);
-    if (lane == 0) ls = (rv && has_l) ? __ldg(p - 1) : 0.0f;
-    R[0] = ls;
-    R[CPL + 1] = rs;
+    R.l = (lane == 0 && rv && has_l) ? __ldg(p - 1) : 0.0f;
+    R.r = (right_here && rv && has_r) ? __ldg(p + ncols) : 0.0f;
+  };
+  // window row from raw values: neighbours across lanes by shuffles
+  auto finish = [&](float(&Wr)[CPL + 2], const Raw& R) {
+#pragma unroll
+    for (int k = 0; k < CPL; k++) Wr[1 + k] = R.v[k];
+    const float ls = __shfl_up_sync(FULL, R.v[CPL - 1], 1);
+    const float rs = __shfl_down_sync(FULL, R.v[0], 1);
+    Wr[0] = (lane == 0) ? R.l : ls;
+    Wr[CPL + 1] = rs;
     if (right_here) {
-      const float rv_r = (rv && has_r) ? __ldg(p + ncols) : 0.0f;
 #pragma unroll
       for (int k = 0; k <= CPL; k++)
-        if (k == ncols) R[k + 1] = rv_r;
+        if (k == ncols) Wr[k + 1] = R.r;
     }
-    p += d.ldz;
   };
   auto emit_row = [&](const float(&U)[CPL + 2], const float(&M)[CPL + 2], const float(&D)[CPL + 2], int i) {
     if (i >= g.th || ncols == 0) return;
     const uint32_t rm = row_off_mask(i, g.th);
     const bool redge = (i == i_top_edge) || (i == i_bot_edge);
+    uint8_t* rowp = dp + (int64_t)(i - r0) * d.lddir;
 #pragma unroll
     for (int k = 0; k < CPL; k++) {
       if (k < ncols) {
@@ -251,34 +265,23 @@ __device__ __forceinline__ void tile_dirs_from_z(const DemDesc& d, const TileGeo
           code = d8_window_code(U[k], U[k + 1], U[k + 2], M[k], M[k + 1], M[k + 2], D[k], D[k + 1], D[k + 2], rule);
         }
         if (!fin) set_status(status, D8_ERR_NONFINITE);
-        dp[k] = (uint8_t)code;
+        rowp[k] = (uint8_t)code;
         add_cell<T>(word, i * T + jb + k, code, rm | colm[k], true, status);
       }
     }
-    dp += d.lddir;
   };
 
-  load(A, r0 - 1);
-  load(B, r0);
-  // rows in triples so the three row buffers rotate without copies
-  int ii = 0;
-#pragma unroll 1
-  for (; ii + 3 <= ROWS; ii += 3) {
-    load(C, r0 + ii + 1);
-    emit_row(A, B, C, r0 + ii);
-    load(A, r0 + ii + 2);
-    emit_row(B, C, A, r0 + ii + 1);
-    load(B, r0 + ii + 3);
-    emit_row(C, A, B, r0 + ii + 2);
-  }
-  if (ii < ROWS) {  // window: A = row above, B = own row
-    load(C, r0 + ii + 1);
-    emit_row(A, B, C, r0 + ii);
-    ii++;
-    if (ii < ROWS) {
-      load(A, r0 + ii + 1);
-      emit_row(B, C, A, r0 + ii);
-    }
+  // software pipeline, fully unrolled: rows are loaded PD steps before use and
+  // the three window rows rotate by register renaming
+  Raw raw[NR];
+  float win[3][CPL + 2];
+#pragma unroll
+  for (int q = 0; q < PD && q < NR; q++) issue(raw[q], q);
+#pragma unroll
+  for (int q = 0; q < NR; q++) {
+    if (q + PD < NR) issue(raw[q + PD], q + PD);
+    finish(win[q % 3], raw[q]);
+    if (q >= 2) emit_row(win[(q + 1) % 3], win[(q + 2) % 3], win[q % 3], r0 + q - 2);
   }
 }
 
@@ -287,19 +290,31 @@ __device__ __forceinline__ void tile_dirs_from_z(const DemDesc& d, const TileGeo
 template <int T>
 __device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const TileGeo& g, uint32_t* word,
                                                     uint32_t* status) {
+  constexpr int NQ = T * T / 4 / NTU;  // four-cell groups per thread
   const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
-  for (int q = threadIdx.x; q < T * T / 4; q += NTU) {
+  // issue every load of this thread before using any (hides the memory latency)
+  uint32_t fours[NQ];
+#pragma unroll
+  for (int r = 0; r < NQ; r++) {
+    const int c = (threadIdx.x + r * NTU) * 4, i = c / T, j = c - i * T;
+    fours[r] = 0;
+    if (i < g.th) {
+      const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
+      if (vec) {
+        fours[r] = __ldg(reinterpret_cast<const unsigned int*>(src));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          if (j + k < g.tw) fours[r] |= (uint32_t)src[k] << (8 * k);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NQ; r++) {
+    const int q = threadIdx.x + r * NTU;
     const int c = q * 4, i = c / T, j = c - i * T;
     if (i >= g.th) continue;
-    const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
-    uint32_t four = 0;
-    if (vec) {
-      four = *reinterpret_cast<const uint32_t*>(src);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; k++)
-        if (j + k < g.tw) four |= (uint32_t)src[k] << (8 * k);
-    }
+    const uint32_t four = fours[r];
     const uint32_t rm = row_off_mask(i, g.th);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -333,8 +348,29 @@ __device__ __forceinline__ int warp_sources(const uint32_t* word, uint16_t* srcl
   return n;
 }
 
+// A[tile] = the in-tile counts held in word[], four consecutive cells per
+// thread per step (one 16-byte store when the layout allows).
+template <int T>
+__device__ __forceinline__ void store_counts(const DemDesc& d, const TileGeo& g, const uint32_t* word) {
+  for (int q = threadIdx.x; q < T * T / 4; q += NTU) {
+    const int c = q * 4, i = c / T, j = c - i * T;
+    if (i >= g.th) continue;
+    uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
+    const uint4 wq = reinterpret_cast<const uint4*>(word)[q];
+    const uint4 o = make_uint4(w_cnt(wq.x), w_cnt(wq.y), w_cnt(wq.z), w_cnt(wq.w));
+    if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+      *reinterpret_cast<uint4*>(dst) = o;
+    } else {
+      const uint32_t ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (j + k < g.tw) dst[k] = ov[k];
+    }
+  }
+}
+
 template <int T, bool FROM_Z>
-__global__ void __launch_bounds__(NTU) k_up_unit(DemTable dt, Pipe p, int rule) {
+__global__ void __launch_bounds__(NTU, 7) k_up_unit(DemTable dt, Pipe p, int rule) {
   using L = UpLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint32_t* word = reinterpret_cast<uint32_t*>(sm + L::off_word);
@@ -374,44 +410,58 @@ __global__ void __launch_bounds__(NTU) k_up_unit(DemTable dt, Pipe p, int rule) 
       uint32_t acc = 0, wv = 0;
       const unsigned lt = (1u << lane) - 1u;
       for (;;) {
-        while (head >= nsrc && li + NWALK < NWU) {  // next list of this walker
-          li += NWALK;
-          pool = reinterpret_cast<uint16_t*>(sm + L::off_src) + li * (TT / NWU);
-          nsrc = misc[4 + li];
-          head = 0;
+        if (NWALK < NWU) {
+          while (head >= nsrc && li + NWALK < NWU) {  // next list of this walker
+            li += NWALK;
+            pool = reinterpret_cast<uint16_t*>(sm + L::off_src) + li * (TT / NWU);
+            nsrc = misc[4 + li];
+            head = 0;
+          }
         }
+        const unsigned need = __ballot_sync(FULL, cur < 0);
         if (head < nsrc) {
-          const unsigned need = __ballot_sync(FULL, cur < 0);
           const int idx = head + __popc(need & lt);
           if (cur < 0 && idx < nsrc) {
             cur = pool[idx];
             h = cur;
             wv = word[cur];
             acc = w_cnt(wv);
-            done++;
+            if (!FROM_Z) done++;
           }
           head += __popc(need);
-        } else if (!__any_sync(FULL, cur >= 0)) {
+        } else if (need == FULL) {
           break;
         }
-        const bool act = cur >= 0;
-        const bool in = act && (wv & W_IN);
-        const int s = cur + toff_tab<T>(w_code(wv) & 7);
-        uint32_t old = 0;
-        if (in) old = atomicAdd(&word[s], acc + 0xFFFF0000u);
-        const bool cont = in && (w_left(old) == 1u);
-        if (cont) seg[s] = (uint16_t)h;
-        if (act && !cont) seg[h] = in ? (uint16_t)(SEG_REC | s) : (uint16_t)(SEG_REC | SEG_END | cur);
-        done += cont ? 1 : 0;
-        acc = cont ? acc + w_cnt(old) : acc;
-        wv = cont ? old : wv;
-        cur = cont ? s : -1;
+        if (cur >= 0) {
+          if (wv & W_IN) {
+            const int s = cur + toff_tab<T>(w_code(wv));
+            const uint32_t old = atomicAdd(&word[s], acc + 0xFFFF0000u);
+            if (w_left(old) == 1u) {  // last input to arrive: continue there
+              seg[s] = (uint16_t)h;
+              acc += w_cnt(old);
+              wv = old;
+              cur = s;
+              if (!FROM_Z) done++;
+            } else {
+              seg[h] = (uint16_t)(SEG_REC | s);
+              cur = -1;
+            }
+          } else {
+            seg[h] = (uint16_t)(SEG_REC | SEG_END | cur);
+            cur = -1;
+          }
+        }
       }
     }
-    atomicAdd(&misc[0], done);
+    // directions derived from elevations descend strictly, so only a given
+    // direction field can hold a cycle (cells never finished)
+    if (!FROM_Z) atomicAdd(&misc[0], done);
     __syncthreads();
-    const bool cyc = misc[0] != g.th * g.tw;
+    const bool cyc = !FROM_Z && misc[0] != g.th * g.tw;
     if (threadIdx.x == 0 && cyc) set_status(p.status, D8_ERR_CYCLE);
+    // in-tile counts (inflow from other tiles = 0) go to A now; the finalising
+    // pass adds the inflow only where some reaches
+    store_counts<T>(d, g, word);
     // perimeter summary: the exit of each perimeter cell's in-tile path, by a
     // chase over segment records (resolved records are written back)
     for (int s = threadIdx.x; s < 4 * T; s += NTU) {
@@ -449,31 +499,57 @@ __global__ void __launch_bounds__(NTU) k_up_unit(DemTable dt, Pipe p, int rule) 
   }
 }
 
+// Algorithms 7-8 restricted to where they change anything.  A already holds
+// the in-tile counts; the final count is A(c) + F(c), where F(c) is the
+// inflow from other tiles routed through c.  Inflow enters a tile only at its
+// receivers (perimeter cells with an up-slope neighbour in another tile) and
+// follows the unique down-slope path from there, so F(c) is the sum of the
+// receivers' inflows over the receivers whose in-tile path passes through c.
+// Each receiver therefore walks its path once adding its inflow to every cell
+// on it: additions commute, so the walks need no ordering between them and
+// no reply from the shared atomics, and only the cells down-slope of a
+// receiver (about a sixth of a 64 x 64 tile on fractal terrain) are touched.
+// The work is the summed length of the receivers' in-tile paths (at most
+// 4T * T^2 for adversarial fields, about the sub-forest size on terrain).
 template <int T>
-__global__ void __launch_bounds__(NTU) k_down_unit(DemTable dt, Pipe p) {
-  using L = DownLayout<T>;
+__global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
+  using L = FinLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
-  uint32_t* word = reinterpret_cast<uint32_t*>(sm + L::off_word);
-  uint32_t* inf = reinterpret_cast<uint32_t*>(sm + L::off_inf);
-  uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src) + (threadIdx.x >> 5) * (T * T / NWU);
+  uint32_t* F = reinterpret_cast<uint32_t*>(sm + L::off_f);
+  uint8_t* code = sm + L::off_code;
+  uint16_t* rcell = reinterpret_cast<uint16_t*>(sm + L::off_rcell);
+  uint32_t* rin = reinterpret_cast<uint32_t*>(sm + L::off_rin);
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
   const uint32_t* xval = static_cast<const uint32_t*>(p.S);
   constexpr int TT = T * T;
-  const int lane = threadIdx.x & 31;
+
+  // F[] starts at zero; every tile leaves it at zero again (the output pass
+  // clears the words the walks touched)
+  for (int c = threadIdx.x; c < TT / 4; c += NTU) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
+  if (threadIdx.x == 0) misc[0] = 0;
 
   for (int64_t t = next_tile(p.queue + 1); t < p.ntiles; t = next_tile(p.queue + 1)) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
-    uint4* w4 = reinterpret_cast<uint4*>(word);
-    uint4* i4 = reinterpret_cast<uint4*>(inf);
-    for (int c = threadIdx.x; c < TT / 4; c += NTU) {
-      w4[c] = make_uint4(0, 0, 0, 0);
-      i4[c] = make_uint4(0, 0, 0, 0);
+    // the tile's codes (cells outside a ragged tile are never reached)
+    {
+      const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
+      for (int q = threadIdx.x; q < TT / 4; q += NTU) {
+        const int c = q * 4, i = c / T, j = c - i * T;
+        if (i >= g.th) continue;
+        const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
+        uint32_t four = 0x08080808u;
+        if (vec) {
+          four = __ldg(reinterpret_cast<const unsigned int*>(src));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (j + k < g.tw) four = (four & ~(0xFFu << (8 * k))) | ((uint32_t)src[k] << (8 * k));
+        }
+        reinterpret_cast<uint32_t*>(code)[q] = four;
+      }
     }
-    __syncthreads();
-    tile_codes_from_dir<T>(d, g, word, p.status);
-    // Algorithm 7: resolved inflow from neighbouring tiles' exits seeds the
-    // perimeter cells (carrier count 1 marks the seed)
+    // Algorithm 7: the receivers and their resolved inflow, listed
     for (int s = threadIdx.x; s < 4 * T; s += NTU) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
@@ -488,83 +564,52 @@ __global__ void __launch_bounds__(NTU) k_down_unit(DemTable dt, Pipe p) {
         in += xval[global_slot(d, gi, gj, T)];
       }
       if (in) {
-        inf[i * T + j] = in;
-        atomicAdd(&word[i * T + j], W_INF1);
+        const int r = atomicAdd(&misc[0], 1);
+        rcell[r] = (uint16_t)(i * T + j);
+        rin[r] = in;
       }
     }
     __syncthreads();
-    // Algorithm 8: the same walks, carrying the inflow alongside the count
-    {
-      const int n = warp_sources<T>(word, srcl);
-      if (lane == 0) misc[4 + (threadIdx.x >> 5)] = n;
-    }
-    __syncthreads();
-    if ((threadIdx.x >> 5) < NWALK) {
-      int li = threadIdx.x >> 5, head = 0, cur = -1;
-      const uint16_t* pool = reinterpret_cast<uint16_t*>(sm + L::off_src) + li * (TT / NWU);
-      int nsrc = misc[4 + li];
-      uint32_t acc = 0, wv = 0, fl = 0;
-      const unsigned lt = (1u << lane) - 1u;
-      for (;;) {
-        while (head >= nsrc && li + NWALK < NWU) {
-          li += NWALK;
-          pool = reinterpret_cast<uint16_t*>(sm + L::off_src) + li * (TT / NWU);
-          nsrc = misc[4 + li];
-          head = 0;
-        }
-        if (head < nsrc) {
-          const unsigned need = __ballot_sync(FULL, cur < 0);
-          const int idx = head + __popc(need & lt);
-          if (cur < 0 && idx < nsrc) {
-            cur = pool[idx];
-            wv = word[cur];
-            acc = w_cnt(wv);
-            fl = w_inf(wv) ? inf[cur] : 0u;
-          }
-          head += __popc(need);
-        } else if (!__any_sync(FULL, cur >= 0)) {
-          break;
-        }
-        const bool act = cur >= 0;
-        const bool in = act && (wv & W_IN);
-        const int s = cur + toff_tab<T>(w_code(wv) & 7);
-        uint32_t add = acc + 0xFFFF0000u;
-        if (in && fl) {  // publish the carried inflow before the count update
-          atomicAdd(&inf[s], fl);
-          __threadfence_block();
-          add += W_INF1;
-        }
-        uint32_t old = 0;
-        if (in) old = atomicAdd(&word[s], add);
-        const bool cont = in && (w_left(old) == 1u);
-        const uint32_t nw = old + add;
-        if (cont && w_inf(nw)) {  // some input carried inflow: read the total
-          __threadfence_block();
-          fl = inf[s];
-        } else if (cont) {
-          fl = 0;
-        }
-        acc = cont ? acc + w_cnt(old) : acc;
-        wv = cont ? nw : wv;
-        cur = cont ? s : -1;
+    const int nrec = misc[0];
+    // Algorithm 8 on the receivers' paths (a path inside one tile has at most
+    // T^2 cells; the bound only matters for a field with a cycle, which the
+    // first pass reports)
+    for (int r = threadIdx.x; r < nrec; r += NTU) {
+      const uint32_t in = rin[r];
+      int c = rcell[r], i = c / T, j = c & (T - 1);
+      atomicAdd(&F[c], in);
+      for (int step = 0; step < TT; step++) {
+        const int k = code[c];
+        if (k >= 8) break;
+        i += code_di(k);
+        j += code_dj(k);
+        if ((unsigned)i >= (unsigned)g.th || (unsigned)j >= (unsigned)g.tw) break;
+        c = i * T + j;
+        atomicAdd(&F[c], in);
       }
     }
     __syncthreads();
-    // final counts, four consecutive cells per thread per step
+    if (threadIdx.x == 0) misc[0] = 0;
+    // A += F where F is nonzero; touched words go back to zero
     for (int q = threadIdx.x; q < TT / 4; q += NTU) {
+      const uint4 f = reinterpret_cast<const uint4*>(F)[q];
+      if (!(f.x | f.y | f.z | f.w)) continue;
+      reinterpret_cast<uint4*>(F)[q] = make_uint4(0, 0, 0, 0);
       const int c = q * 4, i = c / T, j = c - i * T;
       if (i >= g.th) continue;
       uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
-      const uint4 wq = reinterpret_cast<const uint4*>(word)[q];
-      const uint4 iq = reinterpret_cast<const uint4*>(inf)[q];
-      const uint4 o = make_uint4(w_cnt(wq.x) + iq.x, w_cnt(wq.y) + iq.y, w_cnt(wq.z) + iq.z, w_cnt(wq.w) + iq.w);
       if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-        *reinterpret_cast<uint4*>(dst) = o;
+        uint4 a = *reinterpret_cast<uint4*>(dst);
+        a.x += f.x;
+        a.y += f.y;
+        a.z += f.z;
+        a.w += f.w;
+        *reinterpret_cast<uint4*>(dst) = a;
       } else {
-        const uint32_t ov[4] = {o.x, o.y, o.z, o.w};
+        const uint32_t fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
         for (int k = 0; k < 4; k++)
-          if (j + k < g.tw) dst[k] = ov[k];
+          if (j + k < g.tw && fv[k]) dst[k] += fv[k];
       }
     }
   }
@@ -595,10 +640,10 @@ static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, int rule,
 
 template <int T>
 static cudaError_t launch_down_unit_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
-  const size_t bytes = DownLayout<T>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_down_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const size_t bytes = FinLayout<T>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_fin_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_down_unit<T><<<persistent_grid_u(k_down_unit<T>, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
+  k_fin_unit<T><<<persistent_grid_u(k_fin_unit<T>, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
