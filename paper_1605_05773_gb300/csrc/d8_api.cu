@@ -275,7 +275,7 @@ DemTable single(const DemDesc& d) {
 
 bool slots_fit(int64_t ntiles, int T) { return (uint64_t)ntiles * 4 * (uint64_t)T < 0xFFFFFFF0ull; }
 
-// forward pipeline on one DEM: tile pass (with fused directions when z given),
+// forward pipeline on one DEM: directions (when z is given), tile pass,
 // combine, finalise
 d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStream_t s) {
   const int T = c->T;
@@ -297,6 +297,12 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   Pipe p = carve_pipe(c->ws, ntiles, T, vb, c->status);
   DemTable dt = single(d);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (mode == UP_UNIT_Z) {
+    StageScope sc(c, ST_FLOWDIR, s);
+    e = launch_flowdir(dt, ntiles, T, rule, c->status, s, &sc.n);
+    mode = UP_UNIT_DIR;
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   {
     StageScope sc(c, ST_UP, s);

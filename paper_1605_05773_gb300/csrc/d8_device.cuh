@@ -30,40 +30,6 @@ __device__ __forceinline__ int opposite(int k) { return (k + 4) & 7; }
 // fp32 nearest 1/sqrt(2): the diagonal distance factor of the steepest rule
 __device__ __forceinline__ float inv_sqrt2_f32() { return __uint_as_float(0x3F3504F3u); }
 
-// D8 code of an interior cell whose 3x3 neighbourhood is z[(r-1..r+1)*ld + (c-1..c+1)].
-// Steepest ("The Algorithm"): slope = drop for cardinals, drop * (1/sqrt 2) for
-// diagonals, one rounded fp32 multiply; lowest ("Introduction"): smallest z.
-// Strict comparisons in N..NW order, so the first of equal candidates wins and
-// only strictly lower neighbours count; none gives SINK (9).
-__device__ __forceinline__ int d8_code_interior(const float* z, int ld, int r, int c, int rule) {
-  const float zc = z[r * ld + c];
-  int bk = 9;
-  if (rule == 0) {
-    const float R = inv_sqrt2_f32();
-    float best = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const float zn = z[(r + code_di(k)) * ld + (c + code_dj(k))];
-      const float d = __fsub_rn(zc, zn);
-      const float s = (k & 1) ? __fmul_rn(d, R) : d;
-      if (s > best) {
-        best = s;
-        bk = k;
-      }
-    }
-  } else {
-    float best = zc;
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const float zn = z[(r + code_di(k)) * ld + (c + code_dj(k))];
-      if (zn < best) {
-        best = zn;
-        bk = k;
-      }
-    }
-  }
-  return bk;
-}
 
 // ---- compensated fp32 ("float-float") ------------------------------------
 struct ff {

@@ -1,21 +1,23 @@
-// d8_fwd.cu -- forward kernels of libd8.
+// d8_fwd.cu -- the weighted forward pipeline and the flat combine of libd8.
 //
-//  k_flowdir  D8 direction stencil ("The Algorithm": steepest slope over the
-//             eight neighbours; "Introduction": lowest neighbour).
-//  k_up       per tile ("slave partition"): directions (fused) or codes, the
-//             in-tile dependency count (Algorithm 1), the in-tile up-slope area
-//             with inflow from other tiles treated as unknown = 0 (Algorithms
-//             2-4), and the perimeter summary: for every perimeter cell the
-//             perimeter cell where its in-tile path leaves the tile (the
-//             exit-side view of Cell_V / Origin) and the in-tile area.
-//  k_pj_*     the combine (Algorithms 5-6): the exits of all tiles form a
-//             forest (an exit's parent is the exit its path reaches next); its
-//             subtree sums are found by pointer jumping with scatter-adds,
-//             ceil(log2(depth)) rounds.
-//  k_down     per tile finalise (Algorithms 7-8): every perimeter cell gets
-//             the resolved inflow from the exits of neighbouring tiles that
-//             drain into it, then the in-tile accumulation is re-run with
-//             those seeds and the final areas are written.
+//  k_up       per tile ("slave partition"), weighted: the in-tile dependency
+//             count (Algorithm 1), the in-tile up-slope area with inflow from
+//             other tiles treated as unknown = 0 (Algorithms 2-4), and the
+//             perimeter summary: for every perimeter cell the perimeter cell
+//             where its in-tile path leaves the tile (the exit-side view of
+//             Cell_V / Origin) and the in-tile area.
+//  k_pj_*     the flat combine (Algorithms 5-6): the exits of all tiles form
+//             a forest (an exit's parent is the exit its path reaches next);
+//             its subtree sums are found by pointer jumping with scatter-adds,
+//             ceil(log2(depth)) rounds.  Used by the weighted pipeline and,
+//             with uint32 values, by the allocation-free entry point.
+//  k_down     per tile finalise, weighted (Algorithms 7-8): every perimeter
+//             cell gets the resolved inflow from the exits of neighbouring
+//             tiles that drain into it, then the in-tile accumulation is
+//             re-run with those seeds and the final areas are written.
+//
+// The unit-count tile passes live in d8_unit.cu, the direction stencil in
+// d8_flowdir.cu; launch_up and launch_down route the unit modes there.
 //
 // The in-tile accumulation is the paper's queue method in shared memory: each
 // cell counts its in-tile inputs (and remembers which neighbours they are),
@@ -32,13 +34,10 @@ namespace d8 {
 // ---------------------------------------------------------------------------
 // shared-memory layouts
 
-template <int T, class V, bool FROM_Z>
+template <int T, class V>
 struct UpLayout {
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t zs_bytes = FROM_Z ? (size_t)(T + 2) * (T + 2) * 4 : 0;
-  static constexpr size_t jp_bytes = TT * 2;
-  static constexpr size_t r0 = ((zs_bytes > jp_bytes ? zs_bytes : jp_bytes) + 15) / 16 * 16;
-  static constexpr size_t off_dm = r0;
+  static constexpr size_t off_dm = (TT * 2 + 15) / 16 * 16;  // after jp (uint16 per cell)
   static constexpr size_t off_val = off_dm + TT * 4;
   static constexpr size_t off_cl = off_val + TT * sizeof(V);
   static constexpr size_t off_misc = off_cl + (TT + 15) / 16 * 16;
@@ -75,32 +74,6 @@ __device__ __forceinline__ void store_out(const DemDesc& d, int64_t gi, int64_t 
 
 // ---------------------------------------------------------------------------
 // in-tile building blocks
-
-// Load the T x T tile of z plus a one-cell halo into zs[(T+2) x (T+2)].
-template <int T>
-__device__ __forceinline__ void load_z_halo(float* zs, const DemDesc& d, const TileGeo& g) {
-  constexpr int ZS = T + 2;
-  for (int idx = threadIdx.x; idx < ZS * ZS; idx += NT) {
-    const int r = idx / ZS, c = idx - r * ZS;
-    const int64_t gi = g.i0 + r - 1, gj = g.j0 + c - 1;
-    float v = 0.0f;
-    if (r <= g.th + 1 && c <= g.tw + 1 && gi >= 0 && gj >= 0 && gi < d.H && gj < d.W) v = d.z[gi * d.ldz + gj];
-    zs[idx] = v;
-  }
-}
-
-// D8 code of tile cell (i, j) from the halo tile (edge cells are OUTLET).
-template <int T>
-__device__ __forceinline__ int code_from_z(const float* zs, const DemDesc& d, const TileGeo& g, int i, int j,
-                                           int rule, uint32_t* status) {
-  const int64_t gi = g.i0 + i, gj = g.j0 + j;
-  const float zc = zs[(i + 1) * (T + 2) + (j + 1)];
-  const bool fin = isfinite(zc);
-  if (!fin) set_status(status, D8_ERR_NONFINITE);
-  if (gi == 0 || gj == 0 || gi == d.H - 1 || gj == d.W - 1) return 8;
-  if (!fin) return 9;
-  return d8_code_interior(zs, T + 2, i + 1, j + 1, rule);
-}
 
 // In-tile dependency counts (Algorithm 1): dm[c] bits 0..7 = number of
 // in-tile inputs, bits 8..15 = which neighbours (by direction from c) they are.
@@ -195,32 +168,11 @@ __device__ __forceinline__ int find_exit(volatile uint16_t* jp, int c, uint32_t*
 // ---------------------------------------------------------------------------
 // kernels
 
-template <int T>
-__global__ void __launch_bounds__(NT) k_flowdir(DemTable dt, int64_t ntiles, int rule, uint32_t* status,
-                                                 uint32_t* queue) {
+template <int T, class V>
+__global__ void __launch_bounds__(NT) k_up(DemTable dt, Pipe p) {
+  using L = UpLayout<T, V>;
   extern __shared__ __align__(16) unsigned char sm[];
-  float* zs = reinterpret_cast<float*>(sm);
-  for (int64_t t = next_tile(queue); t < ntiles; t = next_tile(queue)) {
-    const DemDesc d = dem_of(dt, t);
-    const TileGeo g = tile_geo(d, t - d.tile_base, T);
-    load_z_halo<T>(zs, d, g);
-    __syncthreads();
-    for (int c = threadIdx.x; c < T * T; c += NT) {
-      const int i = c / T, j = c - i * T;
-      if (i >= g.th || j >= g.tw) continue;
-      d.dir[(g.i0 + i) * d.lddir + g.j0 + j] = (uint8_t)code_from_z<T>(zs, d, g, i, j, rule, status);
-    }
-    __syncthreads();
-  }
-}
-
-template <int T, class V, int MODE>
-__global__ void __launch_bounds__(NT) k_up(DemTable dt, Pipe p, int rule) {
-  constexpr bool FROM_Z = (MODE == UP_UNIT_Z);
-  using L = UpLayout<T, V, FROM_Z>;
-  extern __shared__ __align__(16) unsigned char sm[];
-  float* zs = reinterpret_cast<float*>(sm);
-  uint16_t* jp = reinterpret_cast<uint16_t*>(sm);  // aliases zs once directions are known
+  uint16_t* jp = reinterpret_cast<uint16_t*>(sm);
   uint32_t* dm = reinterpret_cast<uint32_t*>(sm + L::off_dm);
   V* val = reinterpret_cast<V*>(sm + L::off_val);
   uint8_t* cl = sm + L::off_cl;
@@ -231,10 +183,6 @@ __global__ void __launch_bounds__(NT) k_up(DemTable dt, Pipe p, int rule) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     if (threadIdx.x == 0) misc[0] = 0;
-    if (FROM_Z) {
-      load_z_halo<T>(zs, d, g);
-      __syncthreads();
-    }
     // codes, classes and seeds
     for (int c = threadIdx.x; c < T * T; c += NT) {
       const int i = c / T, j = c - i * T;
@@ -244,14 +192,7 @@ __global__ void __launch_bounds__(NT) k_up(DemTable dt, Pipe p, int rule) {
         continue;
       }
       const int64_t gi = g.i0 + i, gj = g.j0 + j;
-      int code;
-      if (FROM_Z) {
-        code = code_from_z<T>(zs, d, g, i, j, rule, p.status);
-        d.dir[gi * d.lddir + gj] = (uint8_t)code;
-      } else {
-        code = d.dir[gi * d.lddir + gj];
-      }
-      cl[c] = classify(code, i, j, g, d, p.status);
+      cl[c] = classify(d.dir[gi * d.lddir + gj], i, j, g, d, p.status);
       val[c] = seed_of<V>(d, gi, gj);
     }
     __syncthreads();
@@ -461,78 +402,55 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// shared memory of the weighted tile kernels (the unit-count kernels always fit)
 size_t up_smem_bytes(int T, int mode) {
-  const bool z = (mode == UP_UNIT_Z);
-  const bool w = (mode == UP_WEIGHTED);
+  if (mode != UP_WEIGHTED) return (T == 32 || T == 64 || T == 128) ? 1 : 0;
   size_t b = 0;
   switch (T) {
-    case 32: b = w ? UpLayout<32, ff, false>::bytes : (z ? UpLayout<32, uint32_t, true>::bytes : UpLayout<32, uint32_t, false>::bytes); break;
-    case 64: b = w ? UpLayout<64, ff, false>::bytes : (z ? UpLayout<64, uint32_t, true>::bytes : UpLayout<64, uint32_t, false>::bytes); break;
-    case 128: b = w ? UpLayout<128, ff, false>::bytes : (z ? UpLayout<128, uint32_t, true>::bytes : UpLayout<128, uint32_t, false>::bytes); break;
+    case 32: b = UpLayout<32, ff>::bytes; break;
+    case 64: b = UpLayout<64, ff>::bytes; break;
+    case 128: b = UpLayout<128, ff>::bytes; break;
     default: return 0;
   }
   return b <= 227 * 1024 ? b : 0;
 }
 
 size_t down_smem_bytes(int T, bool weighted) {
+  if (!weighted) return (T == 32 || T == 64 || T == 128) ? 1 : 0;
   size_t b = 0;
   switch (T) {
-    case 32: b = weighted ? DownLayout<32, ff>::bytes : DownLayout<32, uint32_t>::bytes; break;
-    case 64: b = weighted ? DownLayout<64, ff>::bytes : DownLayout<64, uint32_t>::bytes; break;
-    case 128: b = weighted ? DownLayout<128, ff>::bytes : DownLayout<128, uint32_t>::bytes; break;
+    case 32: b = DownLayout<32, ff>::bytes; break;
+    case 64: b = DownLayout<64, ff>::bytes; break;
+    case 128: b = DownLayout<128, ff>::bytes; break;
     default: return 0;
   }
   return b <= 227 * 1024 ? b : 0;
 }
 
 template <int T>
-static cudaError_t launch_flowdir_t(const DemTable& dt, int64_t ntiles, int rule, uint32_t* status, cudaStream_t s) {
-  const size_t bytes = (size_t)(T + 2) * (T + 2) * 4;
-  cudaError_t e = set_smem(k_flowdir<T>, bytes);
-  if (e != cudaSuccess) return e;
-  uint32_t* queue = status + 1;
-  e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return e;
-  k_flowdir<T><<<persistent_grid(k_flowdir<T>, bytes, ntiles), NT, bytes, s>>>(dt, ntiles, rule, status, queue);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_flowdir(const DemTable& dt, int64_t ntiles, int T, int rule, uint32_t* status, cudaStream_t s,
-                           int* nlaunch) {
-  ++*nlaunch;
-  switch (T) {
-    case 32: return launch_flowdir_t<32>(dt, ntiles, rule, status, s);
-    case 64: return launch_flowdir_t<64>(dt, ntiles, rule, status, s);
-    case 128: return launch_flowdir_t<128>(dt, ntiles, rule, status, s);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int T, class V, int MODE>
-static cudaError_t launch_up_t(const DemTable& dt, const Pipe& p, int rule, cudaStream_t s) {
-  const size_t bytes = UpLayout<T, V, MODE == UP_UNIT_Z>::bytes;
+static cudaError_t launch_up_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
+  const size_t bytes = UpLayout<T, ff>::bytes;
   if (bytes > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = set_smem(k_up<T, V, MODE>, bytes);
+  cudaError_t e = set_smem(k_up<T, ff>, bytes);
   if (e != cudaSuccess) return e;
-  k_up<T, V, MODE><<<persistent_grid(k_up<T, V, MODE>, bytes, p.ntiles), NT, bytes, s>>>(dt, p, rule);
+  k_up<T, ff><<<persistent_grid(k_up<T, ff>, bytes, p.ntiles), NT, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
+// UP_UNIT_Z: directions first (d8_flowdir.cu), then the unit tile pass on them
 cudaError_t launch_up(const DemTable& dt, const Pipe& p, int mode, int rule, cudaStream_t s, int* nlaunch) {
-  ++*nlaunch;
-  if (mode == UP_UNIT_Z || mode == UP_UNIT_DIR) return launch_up_unit(dt, p, mode == UP_UNIT_Z, rule, s);
-#define D8_UP_CASE(TT)                                                                      \
-  case TT:                                                                                  \
-    if (mode == UP_UNIT_Z) return launch_up_t<TT, uint32_t, UP_UNIT_Z>(dt, p, rule, s);     \
-    if (mode == UP_UNIT_DIR) return launch_up_t<TT, uint32_t, UP_UNIT_DIR>(dt, p, rule, s); \
-    if (mode == UP_WEIGHTED) return launch_up_t<TT, ff, UP_WEIGHTED>(dt, p, rule, s);       \
-    return cudaErrorInvalidValue;
-  switch (p.T) {
-    D8_UP_CASE(32)
-    D8_UP_CASE(64)
-    D8_UP_CASE(128)
+  if (mode == UP_UNIT_Z) {
+    const cudaError_t e = launch_flowdir(dt, p.ntiles, p.T, rule, p.status, s, nlaunch);
+    if (e != cudaSuccess) return e;
   }
-#undef D8_UP_CASE
+  ++*nlaunch;
+  if (mode == UP_UNIT_Z || mode == UP_UNIT_DIR) return launch_up_unit(dt, p, s);
+  if (mode != UP_WEIGHTED) return cudaErrorInvalidValue;
+  switch (p.T) {
+    case 32: return launch_up_t<32>(dt, p, s);
+    case 64: return launch_up_t<64>(dt, p, s);
+    case 128: return launch_up_t<128>(dt, p, s);
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -577,9 +495,9 @@ cudaError_t launch_down(const DemTable& dt, const Pipe& p, bool weighted, cudaSt
   ++*nlaunch;
   if (!weighted) return launch_down_unit(dt, p, s);
   switch (p.T) {
-    case 32: return weighted ? launch_down_t<32, ff>(dt, p, s) : launch_down_t<32, uint32_t>(dt, p, s);
-    case 64: return weighted ? launch_down_t<64, ff>(dt, p, s) : launch_down_t<64, uint32_t>(dt, p, s);
-    case 128: return weighted ? launch_down_t<128, ff>(dt, p, s) : launch_down_t<128, uint32_t>(dt, p, s);
+    case 32: return launch_down_t<32, ff>(dt, p, s);
+    case 64: return launch_down_t<64, ff>(dt, p, s);
+    case 128: return launch_down_t<128, ff>(dt, p, s);
   }
   return cudaErrorInvalidValue;
 }

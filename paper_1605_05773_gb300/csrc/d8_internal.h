@@ -35,6 +35,9 @@ struct DemTable {
   int ndem;
 };
 
+// First-pass modes: unit counts from a direction field; unit counts with the
+// directions computed first from z (the direction kernel, then the same tile
+// pass); weighted (float) areas from a direction field.
 enum UpMode { UP_UNIT_DIR = 0, UP_UNIT_Z = 1, UP_WEIGHTED = 2 };
 
 // Device workspace of one pipeline run (all arrays indexed by global slot id
@@ -53,7 +56,7 @@ struct Pipe {
   uint32_t* queue;   // tile work-queue counters (one per stage)
 };
 
-// ---- launchers (d8_fwd.cu / d8_bwd.cu) -------------------------------------
+// ---- launchers (d8_flowdir.cu / d8_fwd.cu / d8_bwd.cu) ---------------------
 // Each enqueues its kernels on `s` and adds the number of kernel launches it
 // made to *nlaunch.
 cudaError_t launch_flowdir(const DemTable& dt, int64_t ntiles, int T, int rule, uint32_t* status, cudaStream_t s,
@@ -99,7 +102,7 @@ int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels);
 cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch);
 
 // unit-count tile passes (d8_unit.cu)
-cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool from_z, int rule, cudaStream_t s);
+cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, cudaStream_t s);
 cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, cudaStream_t s);
 
 // shared-memory bytes of the per-tile kernels (0 = configuration unsupported)

@@ -1,9 +1,9 @@
 // d8_unit.cu -- the unit-count tile passes (the headline path).
 //
-//  k_up_unit    per tile: D8 directions (fused, from z) or codes (from dir),
-//               the in-tile dependency count (Algorithm 1), the in-tile
-//               up-slope counts with inflow from other tiles unknown = 0
-//               (Algorithms 2-4) and the perimeter summary.
+//  k_up_unit    per tile: codes from the direction field, the in-tile
+//               dependency count (Algorithm 1), the in-tile up-slope counts
+//               with inflow from other tiles unknown = 0 (Algorithms 2-4),
+//               written to A, and the perimeter summary.
 //  k_fin_unit   per tile finalise (Algorithms 7-8): A already holds the
 //               in-tile counts; the resolved inflow from neighbouring tiles
 //               is pushed down the in-tile paths it reaches and added there.
@@ -15,21 +15,20 @@
 //    to its down-slope cell and tells the sender whether it was the last
 //    input; only then does the sender continue (Algorithm 2's tail
 //    recursion).  The in-tile count of a 128 x 128 tile fits in 16 bits;
-//  * the first pass writes the in-tile counts to A, so the finalising pass
-//    only walks the paths down-slope of the perimeter cells that receive
-//    inflow from other tiles, adding that inflow along them, instead of
-//    re-running the whole tile;
-//  * one warp spans the tile width, each lane owning T/32 adjacent columns:
-//    it slides a 3-row register window down its columns with vector loads of
-//    z straight from global memory (coalesced), left/right neighbours come
-//    from warp shuffles, and the eight slopes are formed with packed fp32x2
-//    arithmetic (each cardinal neighbour paired with a diagonal);
-//  * each warp draws the starting cells of its walks (sources: no in-tile
-//    input) from its own pool with ballots, without shared atomics;
+//  * the walks are latency-bound, so shared memory per tile is kept small
+//    (the word array, a uint16 segment record per cell and a 64-entry ring
+//    of pending sources per warp: 24.6 KB for 64 x 64) to fit eight tiles per
+//    SM, and the launch bounds hold registers to the same eight;
+//  * each warp feeds idle lanes from its ring with ballots (no shared
+//    atomics), refilling the ring by scanning its own cells as it goes;
 //  * every walk records its segment (the cells it finished) and where the
 //    segment ended (at a tile exit or path end, or at the junction where
 //    another walk took over), so the exit of any perimeter cell's in-tile
-//    path is a short chase over segment records instead of a walk over cells.
+//    path is a short chase over segment records instead of a walk over cells;
+//  * the first pass writes the in-tile counts to A, so the finalising pass
+//    only walks the paths down-slope of the perimeter cells that receive
+//    inflow from other tiles, adding that inflow along them, instead of
+//    re-running the whole tile.
 #include "d8_device.cuh"
 
 namespace d8 {
@@ -37,28 +36,8 @@ namespace unit {
 
 constexpr int NTU = 128;  // threads per tile block (4 warps)
 constexpr int NWU = NTU / 32;
-#ifndef D8_WALK_WARPS
-#define D8_WALK_WARPS 4
-#endif
-// Warps that walk (Algorithm 2).  A walk phase lasts at least as many steps as
-// the longest in-tile flow path (about 1.3 T) whatever the number of walkers;
-// measured on GB300 (64 x 64 tiles) all four warps walking is fastest.
-constexpr int NWALK = D8_WALK_WARPS;
 constexpr unsigned FULL = 0xFFFFFFFFu;
-
-// word: count 0..15 | inputs left 16..19 | code 20..23 | IN 24 | EXIT 25 |
-// PRESENT 26
-constexpr uint32_t W_IN = 1u << 24, W_EXIT = 1u << 25, W_PRES = 1u << 26;
-__device__ __forceinline__ uint32_t w_cnt(uint32_t w) { return w & 0xFFFFu; }
-__device__ __forceinline__ uint32_t w_left(uint32_t w) { return (w >> 16) & 0xFu; }
-__device__ __forceinline__ int w_code(uint32_t w) { return (int)((w >> 20) & 0xFu); }
-
-// Segment records (one uint16 per cell).  A finished non-source cell holds
-// the source cell whose walk finished it.  A source cell holds its walk's end
-// record: SEG_REC | SEG_END | cell (the walk ended at that cell: a tile exit
-// or a path end, told apart by the cell's class bits) or SEG_REC | cell (the
-// walk stopped before that junction cell, which another walk finished).
-constexpr uint16_t SEG_REC = 0x8000u, SEG_END = 0x4000u;
+constexpr int RING = 64;  // pending sources per warp (a power of two > 63)
 
 // In-tile offset of direction k (N, NE, E, SE, S, SW, W, NW) for row stride T.
 // For T <= 64 the eight offsets fit in signed bytes of one 64-bit constant
@@ -73,47 +52,38 @@ __device__ __forceinline__ int toff_tab(int k) {
   return di * T + dj;
 }
 
-// D8 code of an interior cell from its 3x3 window (a = row above, b = own
-// row, c = row below; 0 = left, 1 = centre, 2 = right).
-// Steepest: the slope towards neighbour n is (z - zn) for a cardinal and
-// (z - zn) * R for a diagonal, R = fp32(1/sqrt 2).  Formed here as the exact
-// negations (zn - z) and (zn - z) * R with packed fp32x2 adds/multiplies
-// (cardinal and diagonal of each pair share an instruction; x * 1.0 is
-// exact), and the most negative one wins -- strict comparisons in N..NW
-// order, so ties keep the earlier direction and only a strictly positive
-// drop counts.  Lowest: the smallest neighbour below z, same tie rule.
-__device__ __forceinline__ int d8_window_code(float a0, float a1, float a2, float b0, float b1, float b2, float c0,
-                                              float c1, float c2, int rule) {
-  int code = 9;
-  if (rule == 0) {
-    const float2 nz = make_float2(-b1, -b1);
-    const float2 sc = make_float2(1.0f, inv_sqrt2_f32());
-    const float2 p0 = __fmul2_rn(__fadd2_rn(make_float2(a1, a2), nz), sc);  // N, NE
-    const float2 p1 = __fmul2_rn(__fadd2_rn(make_float2(b2, c2), nz), sc);  // E, SE
-    const float2 p2 = __fmul2_rn(__fadd2_rn(make_float2(c1, c0), nz), sc);  // S, SW
-    const float2 p3 = __fmul2_rn(__fadd2_rn(make_float2(b0, a0), nz), sc);  // W, NW
-    float best = 0.0f;
-    if (p0.x < best) { best = p0.x; code = 0; }
-    if (p0.y < best) { best = p0.y; code = 1; }
-    if (p1.x < best) { best = p1.x; code = 2; }
-    if (p1.y < best) { best = p1.y; code = 3; }
-    if (p2.x < best) { best = p2.x; code = 4; }
-    if (p2.y < best) { best = p2.y; code = 5; }
-    if (p3.x < best) { best = p3.x; code = 6; }
-    if (p3.y < best) { best = p3.y; code = 7; }
-  } else {
-    float best = b1;
-    if (a1 < best) { best = a1; code = 0; }
-    if (a2 < best) { best = a2; code = 1; }
-    if (b2 < best) { best = b2; code = 2; }
-    if (c2 < best) { best = c2; code = 3; }
-    if (c1 < best) { best = c1; code = 4; }
-    if (c0 < best) { best = c0; code = 5; }
-    if (b0 < best) { best = b0; code = 6; }
-    if (a0 < best) { best = a0; code = 7; }
+// The packed per-cell word.  Inputs still to arrive sit in bits 28..31, so
+// one unsigned compare of the value an atomic returns tells the last arriver
+// (left was 1 iff old < 2 << 28); IN (target inside the tile) is bit 25,
+// EXIT (target in another tile) bit 26; the count starts at bit 0.  For
+// T <= 64 the count takes 13 bits and bits 13..24 hold the in-tile index of
+// the down-slope cell (IN cells) or the code (others), so a walk step reads
+// its next cell with one shift and mask.  A 128 x 128 tile needs 15 count
+// bits and an index of 14, so there bits 15..18 hold the code instead and the
+// next cell is computed from it.
+constexpr uint32_t W_IN = 1u << 25, W_EXIT = 1u << 26, W_LEFT1 = 1u << 28;
+template <int T>
+struct WL {
+  static constexpr bool IDX = T <= 64;
+  static constexpr int CB = IDX ? 13 : 15;  // count bits; the next field starts here
+  static constexpr uint32_t CNT = (1u << CB) - 1;
+  static constexpr uint32_t SRC_MASK = 0xF0000000u | CNT;  // a source: count 1, nothing left
+  __device__ static __forceinline__ uint32_t cnt(uint32_t w) { return w & CNT; }
+  __device__ static __forceinline__ bool last(uint32_t old) { return old < 2 * W_LEFT1; }
+  __device__ static __forceinline__ int code(uint32_t w) { return (int)((w >> CB) & 0xFu); }  // non-IN cells
+  __device__ static __forceinline__ int next(uint32_t w, int c) {
+    if (IDX) return (int)((w >> CB) & (uint32_t)(T * T - 1));
+    return c + toff_tab<T>(code(w));
   }
-  return code;
-}
+};
+
+// Segment records (one uint16 per cell).  A finished non-source cell holds
+// the source cell whose walk finished it.  A source cell holds its walk's end
+// record: SEG_REC | SEG_END | cell (the walk ended at that cell: a tile exit
+// or a path end, told apart by the cell's class bits) or SEG_REC | cell (the
+// walk stopped before that junction cell, which another walk finished).
+constexpr uint16_t SEG_REC = 0x8000u, SEG_END = 0x4000u;
+
 
 // Bits of the neighbours of tile cell (i, j) that lie outside a th x tw tile.
 __device__ __forceinline__ uint32_t row_off_mask(int i, int th) {
@@ -124,25 +94,33 @@ __device__ __forceinline__ uint32_t col_off_mask(int j, int tw) {
 }
 
 // Per-cell bookkeeping once its code is known: the cell's own word (count 1,
-// code, class bits) and, when its target is inside the tile, one more input
-// for the target.  A code 0..7 whose target is outside the tile is an exit
-// when the target is on the grid (`grid_target_ok`), otherwise the path ends.
+// next field, class bits) and, when its target is inside the tile, one more
+// input for the target.  A code 0..7 whose target is outside the tile is an
+// exit when the target cell (gi, gj) + offset is on the grid, otherwise the
+// path ends there; that test runs only for those perimeter cells.
 template <int T>
-__device__ __forceinline__ void add_cell(uint32_t* word, int c, int code, uint32_t off_mask, bool grid_target_ok,
-                                         uint32_t* status) {
-  uint32_t cls = 0;
+__device__ __forceinline__ void add_cell(uint32_t* word, int c, int code, uint32_t off_mask, int64_t gi, int64_t gj,
+                                         const DemDesc& d, uint32_t* status) {
+  using W = WL<T>;
+  uint32_t own = 1u;
   if (code < 8) {
     if (!((off_mask >> code) & 1u)) {
-      cls = W_IN;
-      atomicAdd(&word[c + toff_tab<T>(code)], 1u << 16);
-    } else if (grid_target_ok) {
-      cls = W_EXIT;
+      const int t = c + toff_tab<T>(code);
+      atomicAdd(&word[t], W_LEFT1);
+      own |= W_IN | ((uint32_t)(W::IDX ? t : code) << W::CB);
+    } else {
+      const int64_t ti = gi + code_di(code), tj = gj + code_dj(code);
+      if (ti >= 0 && tj >= 0 && ti < d.H && tj < d.W) own |= W_EXIT;
+      own |= (uint32_t)code << W::CB;
     }
-  } else if (code > 9) {
-    set_status(status, D8_ERR_ARG);
-    code = 10;
+  } else {
+    if (code > 9) {
+      set_status(status, D8_ERR_ARG);
+      code = 10;
+    }
+    own |= (uint32_t)code << W::CB;
   }
-  atomicAdd(&word[c], 1u | ((uint32_t)code << 20) | cls | W_PRES);
+  atomicAdd(&word[c], own);
 }
 
 template <int T>
@@ -150,8 +128,8 @@ struct UpLayout {
   static constexpr size_t TT = (size_t)T * T;
   static constexpr size_t off_word = 0;
   static constexpr size_t off_seg = TT * 4;
-  static constexpr size_t off_src = off_seg + TT * 2;
-  static constexpr size_t off_misc = off_src + TT * 2;
+  static constexpr size_t off_ring = off_seg + TT * 2;  // NWU rings of RING entries
+  static constexpr size_t off_misc = off_ring + (size_t)NWU * RING * 2;
   static constexpr size_t bytes = off_misc + 64;
 };
 
@@ -165,125 +143,6 @@ struct FinLayout {
   static constexpr size_t off_misc = off_rin + (size_t)4 * T * 4;
   static constexpr size_t bytes = off_misc + 64;
 };
-
-// Directions of tile g from z into word[] and the dir grid.  One warp spans
-// the tile width; each lane owns CPL = T/32 adjacent columns and walks down
-// ROWS = T/4 rows with a register window of three rows.
-template <int T>
-__device__ __forceinline__ void tile_dirs_from_z(const DemDesc& d, const TileGeo& g, int rule, uint32_t* word,
-                                                 uint32_t* status) {
-  constexpr int CPL = T / 32;
-  constexpr int ROWS = T / NWU;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = warp * ROWS;
-  const int jb = lane * CPL;                      // first own column
-  const int ncols = max(0, min(CPL, g.tw - jb));  // own columns present
-  const int64_t gjb = g.j0 + jb;
-  const bool has_l = gjb >= 1;
-  const bool right_here = ncols > 0 && (jb + CPL >= g.tw);  // owns the tile's last column
-  const bool has_r = g.j0 + g.tw < d.W;
-  const bool vec_ok = (ncols == CPL) && ((reinterpret_cast<uintptr_t>(d.z) & 15u) == 0) && (d.ldz % 4 == 0);
-  const int64_t rows_left = d.H - g.i0;
-  const int i_last = (int)min64(rows_left, (int64_t)T + 1);
-  const int i_first = g.i0 > 0 ? -1 : 0;
-  const int i_top_edge = (g.i0 == 0) ? 0 : -10;
-  const int i_bot_edge = (rows_left <= T) ? (int)rows_left - 1 : -10;
-  uint32_t colm[CPL];
-  bool coledge[CPL];
-#pragma unroll
-  for (int k = 0; k < CPL; k++) {
-    colm[k] = col_off_mask(jb + k, g.tw);
-    const int64_t gj = gjb + k;
-    coledge[k] = (gj == 0) || (gj == d.W - 1);
-  }
-  const float* p0 = d.z + (g.i0 + r0 - 1) * d.ldz + gjb;
-  uint8_t* dp = d.dir + (g.i0 + r0) * d.lddir + gjb;
-
-  // Raw values of one z row for this lane: own columns, plus the column to
-  // the left (lane 0) or right (lane holding the tile's last column).
-  struct Raw {
-    float v[CPL];
-    float l, r;
-  };
-  constexpr int NR = ROWS + 2;  // rows r0-1 .. r0+ROWS
-  constexpr int PD = 4;         // rows loaded ahead of use
-  auto issue = [&](Raw& R, int q) {
-    const int li = r0 - 1 + q;
-    const bool rv = (li >= i_first) && (li < i_last) && ncols > 0;
-    const float* p = p0 + (int64_t)q * d.ldz;
-    if (vec_ok) {
-      if (CPL == 4) {
-        const float4 t = rv ? __ldg(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        R.v[0] = t.x;
-        R.v[CPL > 1 ? 1 : 0] = t.y;
-        R.v[CPL > 2 ? 2 : 0] = t.z;
-        R.v[CPL > 3 ? 3 : 0] = t.w;
-      } else if (CPL == 2) {
-        const float2 t = rv ? __ldg(reinterpret_cast<const float2*>(p)) : make_float2(0.f, 0.f);
-        R.v[0] = t.x;
-        R.v[CPL > 1 ? 1 : 0] = t.y;
-      } else {
-        R.v[0] = rv ? __ldg(p) : 0.0f;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < CPL; k++) R.v[k] = (rv && k < ncols) ? __ldg(p + k) : 0.0f;
-    }
-    R.l = (lane == 0 && rv && has_l) ? __ldg(p - 1) : 0.0f;
-    R.r = (right_here && rv && has_r) ? __ldg(p + ncols) : 0.0f;
-  };
-  // window row from raw values: neighbours across lanes by shuffles
-  auto finish = [&](float(&Wr)[CPL + 2], const Raw& R) {
-#pragma unroll
-    for (int k = 0; k < CPL; k++) Wr[1 + k] = R.v[k];
-    const float ls = __shfl_up_sync(FULL, R.v[CPL - 1], 1);
-    const float rs = __shfl_down_sync(FULL, R.v[0], 1);
-    Wr[0] = (lane == 0) ? R.l : ls;
-    Wr[CPL + 1] = rs;
-    if (right_here) {
-#pragma unroll
-      for (int k = 0; k <= CPL; k++)
-        if (k == ncols) Wr[k + 1] = R.r;
-    }
-  };
-  auto emit_row = [&](const float(&U)[CPL + 2], const float(&M)[CPL + 2], const float(&D)[CPL + 2], int i) {
-    if (i >= g.th || ncols == 0) return;
-    const uint32_t rm = row_off_mask(i, g.th);
-    const bool redge = (i == i_top_edge) || (i == i_bot_edge);
-    uint8_t* rowp = dp + (int64_t)(i - r0) * d.lddir;
-#pragma unroll
-    for (int k = 0; k < CPL; k++) {
-      if (k < ncols) {
-        const float zc = M[1 + k];
-        const bool fin = isfinite(zc);
-        int code;
-        if (redge || coledge[k]) {
-          code = 8;
-        } else if (!fin) {
-          code = 9;
-        } else {
-          code = d8_window_code(U[k], U[k + 1], U[k + 2], M[k], M[k + 1], M[k + 2], D[k], D[k + 1], D[k + 2], rule);
-        }
-        if (!fin) set_status(status, D8_ERR_NONFINITE);
-        rowp[k] = (uint8_t)code;
-        add_cell<T>(word, i * T + jb + k, code, rm | colm[k], true, status);
-      }
-    }
-  };
-
-  // software pipeline, fully unrolled: rows are loaded PD steps before use and
-  // the three window rows rotate by register renaming
-  Raw raw[NR];
-  float win[3][CPL + 2];
-#pragma unroll
-  for (int q = 0; q < PD && q < NR; q++) issue(raw[q], q);
-#pragma unroll
-  for (int q = 0; q < NR; q++) {
-    if (q + PD < NR) issue(raw[q + PD], q + PD);
-    finish(win[q % 3], raw[q]);
-    if (q >= 2) emit_row(win[(q + 1) % 3], win[(q + 2) % 3], win[q % 3], r0 + q - 2);
-  }
-}
 
 // Codes of tile g from a given direction field into word[], four consecutive
 // cells per thread per step (one 32-bit load when the layout allows).
@@ -320,32 +179,9 @@ __device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const Tile
     for (int k = 0; k < 4; k++) {
       if (j + k >= g.tw) break;
       const int code = (four >> (8 * k)) & 0xFF;
-      bool ok = true;
-      if (code < 8) {
-        const int64_t gi = g.i0 + i + code_di(code), gj = g.j0 + j + k + code_dj(code);
-        ok = gi >= 0 && gj >= 0 && gi < d.H && gj < d.W;
-      }
-      add_cell<T>(word, c + k, code, rm | col_off_mask(j + k, g.tw), ok, status);
+      add_cell<T>(word, c + k, code, rm | col_off_mask(j + k, g.tw), g.i0 + i, g.j0 + j + k, d, status);
     }
   }
-}
-
-// Build this warp's pool: the cells it owns (c = lane + 32*warp + NTU*r) with
-// no in-tile input.  Returns the pool size (warp-uniform).
-template <int T>
-__device__ __forceinline__ int warp_sources(const uint32_t* word, uint16_t* srcl) {
-  const int lane = threadIdx.x & 31;
-  int n = 0;
-#pragma unroll 4
-  for (int r = 0; r < T * T / NTU; r++) {
-    const int c = threadIdx.x + r * NTU;
-    const uint32_t w = word[c];
-    const bool s = (w & W_PRES) && w_left(w) == 0u;
-    const unsigned m = __ballot_sync(FULL, s);
-    if (s) srcl[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)c;
-    n += __popc(m);
-  }
-  return n;
 }
 
 // A[tile] = the in-tile counts held in word[], four consecutive cells per
@@ -357,7 +193,8 @@ __device__ __forceinline__ void store_counts(const DemDesc& d, const TileGeo& g,
     if (i >= g.th) continue;
     uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
     const uint4 wq = reinterpret_cast<const uint4*>(word)[q];
-    const uint4 o = make_uint4(w_cnt(wq.x), w_cnt(wq.y), w_cnt(wq.z), w_cnt(wq.w));
+    using W = WL<T>;
+    const uint4 o = make_uint4(W::cnt(wq.x), W::cnt(wq.y), W::cnt(wq.z), W::cnt(wq.w));
     if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
       *reinterpret_cast<uint4*>(dst) = o;
     } else {
@@ -369,17 +206,19 @@ __device__ __forceinline__ void store_counts(const DemDesc& d, const TileGeo& g,
   }
 }
 
-template <int T, bool FROM_Z>
-__global__ void __launch_bounds__(NTU, 7) k_up_unit(DemTable dt, Pipe p, int rule) {
+template <int T>
+__global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
   using L = UpLayout<T>;
+  using W = WL<T>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint32_t* word = reinterpret_cast<uint32_t*>(sm + L::off_word);
   uint16_t* seg = reinterpret_cast<uint16_t*>(sm + L::off_seg);
-  uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src) + (threadIdx.x >> 5) * (T * T / NWU);
+  uint16_t* ring = reinterpret_cast<uint16_t*>(sm + L::off_ring) + (threadIdx.x >> 5) * RING;
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
   uint32_t* pval = static_cast<uint32_t*>(p.pval);
   constexpr int TT = T * T;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
 
   for (int64_t t = next_tile(p.queue + 0); t < p.ntiles; t = next_tile(p.queue + 0)) {
     const DemDesc d = dem_of(dt, t);
@@ -388,60 +227,54 @@ __global__ void __launch_bounds__(NTU, 7) k_up_unit(DemTable dt, Pipe p, int rul
     for (int c = threadIdx.x; c < TT / 4; c += NTU) w4[c] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) misc[0] = 0;
     __syncthreads();
-    if (FROM_Z)
-      tile_dirs_from_z<T>(d, g, rule, word, p.status);
-    else
-      tile_codes_from_dir<T>(d, g, word, p.status);
+    tile_codes_from_dir<T>(d, g, word, p.status);  // Algorithm 1
     __syncthreads();
-    // Algorithm 2: every warp lists the sources among its cells; once all lists
-    // are built the walking warps draw from them
-    {
-      const int n = warp_sources<T>(word, srcl);
-      if (lane == 0) misc[4 + (threadIdx.x >> 5)] = n;
-    }
-    __syncthreads();
+    // Algorithm 2.  Every lane walks down-slope from a source while it is the
+    // last input to arrive at the next cell; a lane whose walk stopped takes
+    // the warp's next pending source.  Pending sources sit in a per-warp ring,
+    // refilled by scanning the warp's own cells (c = lane + 32 w + NTU r) a
+    // row at a time with a ballot.  A source is a cell with count 1 and no
+    // input left (an absent cell of a ragged tile has count 0); the word of a
+    // cell whose last input has arrived holds count >= 2, so a scan running
+    // behind the walks never takes it for one.
     int done = 0;
-    if ((threadIdx.x >> 5) < NWALK) {
-      // One iteration = one step for every lane with a cell in hand, written
-      // as straight-line predicated code so the warp never splits.
-      int li = threadIdx.x >> 5, head = 0, cur = -1, h = 0;
-      const uint16_t* pool = reinterpret_cast<uint16_t*>(sm + L::off_src) + li * (TT / NWU);
-      int nsrc = misc[4 + li];
+    {
+      int r = 0, head = 0, tail = 0, cur = -1, h = 0;
       uint32_t acc = 0, wv = 0;
-      const unsigned lt = (1u << lane) - 1u;
       for (;;) {
-        if (NWALK < NWU) {
-          while (head >= nsrc && li + NWALK < NWU) {  // next list of this walker
-            li += NWALK;
-            pool = reinterpret_cast<uint16_t*>(sm + L::off_src) + li * (TT / NWU);
-            nsrc = misc[4 + li];
-            head = 0;
-          }
+        while (tail - head < 32 && r < TT / NTU) {  // at most RING - 1 pending
+          const int c = threadIdx.x + r * NTU;
+          const bool src = (word[c] & W::SRC_MASK) == 1u;
+          const unsigned m = __ballot_sync(FULL, src);
+          if (src) ring[(tail + __popc(m & lt)) & (RING - 1)] = (uint16_t)c;
+          tail += __popc(m);
+          r++;
         }
+        __syncwarp();
         const unsigned need = __ballot_sync(FULL, cur < 0);
-        if (head < nsrc) {
+        if (head < tail) {
           const int idx = head + __popc(need & lt);
-          if (cur < 0 && idx < nsrc) {
-            cur = pool[idx];
+          if (cur < 0 && idx < tail) {
+            cur = ring[idx & (RING - 1)];
             h = cur;
             wv = word[cur];
-            acc = w_cnt(wv);
-            if (!FROM_Z) done++;
+            acc = 1;  // a source
+            done++;
           }
-          head += __popc(need);
+          head = min(head + __popc(need), tail);
         } else if (need == FULL) {
           break;
         }
         if (cur >= 0) {
           if (wv & W_IN) {
-            const int s = cur + toff_tab<T>(w_code(wv));
-            const uint32_t old = atomicAdd(&word[s], acc + 0xFFFF0000u);
-            if (w_left(old) == 1u) {  // last input to arrive: continue there
+            const int s = W::next(wv, cur);
+            const uint32_t old = atomicAdd(&word[s], acc - W_LEFT1);
+            if (W::last(old)) {  // last input to arrive: continue there
               seg[s] = (uint16_t)h;
-              acc += w_cnt(old);
+              acc += W::cnt(old);
               wv = old;
               cur = s;
-              if (!FROM_Z) done++;
+              done++;
             } else {
               seg[h] = (uint16_t)(SEG_REC | s);
               cur = -1;
@@ -453,11 +286,10 @@ __global__ void __launch_bounds__(NTU, 7) k_up_unit(DemTable dt, Pipe p, int rul
         }
       }
     }
-    // directions derived from elevations descend strictly, so only a given
-    // direction field can hold a cycle (cells never finished)
-    if (!FROM_Z) atomicAdd(&misc[0], done);
+    // a cell never finished lies on or below a cycle of the direction field
+    atomicAdd(&misc[0], done);
     __syncthreads();
-    const bool cyc = !FROM_Z && misc[0] != g.th * g.tw;
+    const bool cyc = misc[0] != g.th * g.tw;
     if (threadIdx.x == 0 && cyc) set_status(p.status, D8_ERR_CYCLE);
     // in-tile counts (inflow from other tiles = 0) go to A now; the finalising
     // pass adds the inflow only where some reaches
@@ -471,9 +303,9 @@ __global__ void __launch_bounds__(NTU, 7) k_up_unit(DemTable dt, Pipe p, int rul
       if (slot_cell(s, g.th, g.tw, T, i, j)) {
         const int c = i * T + j;
         const uint32_t w = word[c];
-        pv = w_cnt(w);
+        pv = W::cnt(w);
         if (w & W_EXIT) {
-          pe = (uint16_t)(PEX_EXIT | w_code(w));
+          pe = (uint16_t)(PEX_EXIT | W::code(w));
         } else if ((w & W_IN) && !cyc) {
           volatile uint16_t* vs = seg;
           const uint16_t v = vs[c];
@@ -629,12 +461,12 @@ static unsigned persistent_grid_u(K kernel, size_t smem, int64_t ntiles) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-template <int T, bool FROM_Z>
-static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, int rule, cudaStream_t s) {
+template <int T>
+static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
   const size_t bytes = UpLayout<T>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_up_unit<T, FROM_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_up_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_up_unit<T, FROM_Z><<<persistent_grid_u(k_up_unit<T, FROM_Z>, bytes, p.ntiles), NTU, bytes, s>>>(dt, p, rule);
+  k_up_unit<T><<<persistent_grid_u(k_up_unit<T>, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
@@ -649,11 +481,11 @@ static cudaError_t launch_down_unit_t(const DemTable& dt, const Pipe& p, cudaStr
 
 }  // namespace unit
 
-cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool from_z, int rule, cudaStream_t s) {
+cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, cudaStream_t s) {
   switch (p.T) {
-    case 32: return from_z ? unit::launch_up_unit_t<32, true>(dt, p, rule, s) : unit::launch_up_unit_t<32, false>(dt, p, rule, s);
-    case 64: return from_z ? unit::launch_up_unit_t<64, true>(dt, p, rule, s) : unit::launch_up_unit_t<64, false>(dt, p, rule, s);
-    case 128: return from_z ? unit::launch_up_unit_t<128, true>(dt, p, rule, s) : unit::launch_up_unit_t<128, false>(dt, p, rule, s);
+    case 32: return unit::launch_up_unit_t<32>(dt, p, s);
+    case 64: return unit::launch_up_unit_t<64>(dt, p, s);
+    case 128: return unit::launch_up_unit_t<128>(dt, p, s);
   }
   return cudaErrorInvalidValue;
 }
