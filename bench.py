@@ -1,9 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark: D8 directions + unit up-slope counts on a 32768 x 32768 pit-free
-fractal DEM (1.07 G cells), one fused pipeline per step.
+fractal DEM (1.07 G cells), one pipeline call per step (direction stencil,
+tile pass, combine, finalise).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--tile T]
+                  [--workload NAME] [--tile T] [--no-cpu-baseline] [--no-extras]
 
 Prints ONE JSON line (rank 0).  `value` is cells/s with the DEM resident in
 HBM (device-timed with CUDA events, max over ranks); `e2e` is the same metric
@@ -11,9 +12,13 @@ through the public API with pinned host buffers, host->device copy of z and
 device->host copy of the directions and counts inside the timed region;
 `roofline` is the dominant kernel's algorithmic bytes per launch over its
 event-timed duration against the measured HBM copy bandwidth; `cpu_baseline`
-times the CPU oracle on a bounded crop of the same DEM.  With torchrun (N>1)
-every rank processes its own replica of the workload (independent DEMs, no
-collective on the data path): weak scaling.
+times the CPU oracle on a bounded crop of the same DEM.  On one GPU the line
+also carries `batched` (512 DEMs of uneven sizes in one graph-captured
+persistent pipeline, autotuned tile, beside the same DEMs one call at a time)
+and `fwd_bwd` (weighted forward + backward at 8192 x 8192 beside the plain
+pipeline on the same DEM).  With torchrun (N>1) every rank processes its own
+replica of the workload (independent DEMs, no collective on the data path):
+weak scaling.
 """
 from __future__ import annotations
 
@@ -36,26 +41,33 @@ WORKLOADS = {
     "fractal_8192": (8192, 8192, "8192x8192 fp32 pit-free fractal DEM, steepest rule, unit weights"),
     "fractal_512": (512, 512, "512x512 fp32 pit-free fractal DEM, steepest rule, unit weights"),
 }
-ALG_BYTES = {"tile_up": 5.0, "tile_down": 5.0, "flowdir": 5.0}  # per cell: z in + dir out / dir in + A out
+# Algorithmic bytes per cell of the stages whose traffic does not depend on
+# the data: the direction stencil reads z (4) and writes dir (1); the tile
+# pass reads dir (1) and writes the in-tile counts (4).  The finalising pass
+# reads dir (1) and rewrites A only where inflow from other tiles arrives.
+ALG_BYTES = {"flowdir": 5.0, "tile_up": 5.0}
 PIPE_BYTES = 9.0  # z in (4) + dir out (1) + A out (4) per cell for the whole path
+KERNEL_SOURCE = {"flowdir": "d8_flowdir.cu", "tile_up": "d8_unit.cu", "tile_down": "d8_unit.cu"}
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per cell of a tile kernel from the committed ncu summary, or
-    None when the kernel source changed since that capture."""
+def measured_traffic(stage: str):
+    """DRAM bytes per cell of a stage's kernel from the committed ncu summary,
+    or None when that kernel's source changed since the capture."""
     import hashlib
 
     prof = os.path.join(ROOT, "profiles", "tile_kernels_fractal_8192.md")
-    src = os.path.join(ROOT, "paper_1605_05773_gb300", "csrc", "d8_unit.cu")
+    src = os.path.join(ROOT, "paper_1605_05773_gb300", "csrc", KERNEL_SOURCE.get(stage, ""))
     try:
         text = open(prof).read().split()
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     except OSError:
         return None
-    if "kernel_source_sha1" not in text or text[text.index("kernel_source_sha1") + 1] != sha:
+    ok = any(text[k] == "kernel_source_sha1" and text[k + 1] == KERNEL_SOURCE[stage] and text[k + 2] == sha
+             for k in range(len(text) - 2))
+    if not ok:
         return None
     for k in range(len(text) - 2):
-        if text[k] == "scaled_traffic_bytes_per_cell" and text[k + 1] == kernel:
+        if text[k] == "scaled_traffic_bytes_per_cell" and text[k + 1] == stage:
             return float(text[k + 2])
     return None
 
@@ -192,6 +204,106 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _event_ms(fn, reps, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batched(dev, stream, steps: int):
+    """The 512-DEM batch (sides log-uniform in [128, 4096], aspect up to 1:4)
+    through the graph-captured persistent pipeline with the autotuned tile,
+    beside the same DEMs run one call at a time."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    import demgen
+    import paper_1605_05773_gb300 as lib
+    from tests.gpu_util import recursion_residual_gpu, terminal_sum_gpu
+
+    shapes = demgen.batch_shapes(512)
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:  # the C generator releases the GIL
+        zs = list(ex.map(lambda a: demgen.fractal(a[1][0], a[1][1], seed=2000 + a[0]), enumerate(shapes)))
+    cells = sum(h * w for h, w in shapes)
+    zt = [torch.from_numpy(z).to(dev) for z in zs]
+    del zs
+    dirs = [torch.empty(s, dtype=torch.uint8, device=dev) for s in shapes]
+    As = [torch.empty(s, dtype=torch.uint32, device=dev) for s in shapes]
+    tile, tune_ms = lib.autotune_batch(zt, dirs, As)
+    plan = lib.BatchPlan(shapes, dev)
+    for _ in range(2):
+        plan.run(zt, dirs, As)
+    torch.cuda.synchronize(dev)
+    if lib.get_status(dev) != "OK":
+        raise RuntimeError("batched run: device status")
+    ms = _event_ms(lambda: plan.run(zt, dirs, As), steps, stream)
+    ok = all(recursion_residual_gpu(dirs[k], As[k]) == 0 and terminal_sum_gpu(dirs[k], As[k]) == h * w
+             for k, (h, w) in enumerate(shapes) if k % 32 == 0)
+
+    def one_by_one():
+        for k in range(len(shapes)):
+            lib.flowdir_accumulate(zt[k], "steepest", dir=dirs[k], A=As[k])
+
+    one_by_one()
+    ms_single = _event_ms(one_by_one, 2, stream)
+    plan.close()
+    return {"workload": "batch_512", "description": "512 pit-free fractal DEMs, sides log-uniform in [128, 4096], "
+                                                    "aspect 1:1-1:4, one graph-captured persistent pipeline",
+            "dems": len(shapes), "cells": cells, "tile": tile, "autotune_ms": tune_ms, "steps": steps,
+            "value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms,
+            "unbatched": {"value": cells / (ms_single / 1e3), "ms_per_step": ms_single,
+                          "how": "the same 512 DEMs through d8_flowdir_accumulate, one call per DEM, same tile"},
+            "parity_guard": ok}
+
+
+def run_fwd_bwd(dev, stream, steps: int):
+    """Weighted forward + hand-written backward on the 8192 x 8192 fractal with
+    lognormal weights and normal cotangents, beside the plain unit pipeline on
+    the same DEM."""
+    import torch
+
+    import demgen
+    import paper_1605_05773_gb300 as lib
+
+    n = 8192
+    z = torch.from_numpy(demgen.fractal(n, n)).to(dev)
+    d = lib.flowdir(z)
+    w = torch.from_numpy(demgen.lognormal_weights(n, n, 11)).to(dev)
+    c = torch.from_numpy(demgen.normal_cotangent(n, n, 12)).to(dev)
+    A = torch.empty((n, n), dtype=torch.float32, device=dev)
+    dw = torch.empty((n, n), dtype=torch.float32, device=dev)
+    Au = torch.empty((n, n), dtype=torch.uint32, device=dev)
+    fwd = lambda: lib.accumulate_weighted(d, w, out=A)  # noqa: E731
+    bwd = lambda: lib.accumulate_backward(d, c, out=dw)  # noqa: E731
+    plain = lambda: lib.flowdir_accumulate(z, "steepest", dir=d, A=Au)  # noqa: E731
+    for _ in range(3):
+        fwd()
+        bwd()
+        plain()
+    torch.cuda.synchronize(dev)
+    if lib.get_status(dev) != "OK":
+        raise RuntimeError("fwd/bwd run: device status")
+    ms_fwd = _event_ms(fwd, steps, stream)
+    ms_bwd = _event_ms(bwd, steps, stream)
+    ms_fb = _event_ms(lambda: (fwd(), bwd()), steps, stream)
+    ms_plain = _event_ms(plain, steps, stream)
+    cells = n * n
+    return {"workload": "weighted_8192", "description": "8192x8192 pit-free fractal, fp32 lognormal(0,1) weights, "
+                                                        "fp32 N(0,1) cotangents; weighted forward + backward",
+            "cells": cells, "steps": steps, "value": cells / (ms_fb / 1e3), "unit": "cells/s",
+            "ms_per_step": ms_fb, "fwd_ms": ms_fwd, "bwd_ms": ms_bwd,
+            "plain": {"value": cells / (ms_plain / 1e3), "ms_per_step": ms_plain,
+                      "how": "d8_flowdir_accumulate (unit counts, directions included) on the same DEM"}}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -286,7 +398,8 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs larger than L2 (4.3 GB z per step, 129 MB L2)", "parity_guard": ok},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": (tb * cells if tb else None),
-                         "traffic_note": "ncu dram bytes per cell at 8192^2 (profiles/tile_kernels_fractal_8192.md) x cells",
+                         "traffic_note": "ncu dram bytes per cell at 8192^2 (profiles/tile_kernels_fractal_8192.md) x cells; "
+                                         "null when the kernel changed since that capture",
                          "peak_kind": peak_kind,
                          "alg_bytes_per_cell": ALG_BYTES[dom], "ms_per_launch": dom_ms},
             "pipeline_roofline": {"alg_bytes_per_cell": PIPE_BYTES,
@@ -299,6 +412,11 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "clocks": clk,
         }
+        if world == 1 and not args.no_extras:
+            lib.set_profiling(False, dev)
+            line["batched"] = run_batched(dev, stream, max(3, min(args.steps, 5)))
+            lib.set_tile(args.tile)
+            line["fwd_bwd"] = run_fwd_bwd(dev, stream, max(3, min(args.steps, 10)))
         print(json.dumps(line), flush=True)
     return 0
 
@@ -312,6 +430,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fractal_32768")
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and fwd+bwd lines")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

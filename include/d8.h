@@ -126,6 +126,21 @@ d8_status d8_batch_flowdir_accumulate(d8_batch* plan, const float* const* z, uin
 /* Free a plan (synchronises its stream first).  NULL is a no-op. */
 d8_status d8_batch_destroy(d8_batch* plan);
 
+/* Autotuner for batches: runs d8_batch_flowdir_accumulate on the given batch
+ * (shapes and buffers exactly as for d8_batch_plan and
+ * d8_batch_flowdir_accumulate) with every supported tile side (32, 64, 128),
+ * one untimed run then two timed graph replays each, and keeps the fastest:
+ * *best_tile receives it and the context's tile side is set to it, so a plan
+ * made next uses it.  ms: optional host array of 3 floats receiving the
+ * per-run milliseconds for tiles 32, 64, 128 (-1 where that tile failed).
+ * The paper has no counterpart: its partition size is an input of the method,
+ * and here it is chosen by measurement on the target GPU.  dir and A hold the
+ * results of the last run.  Synchronises `stream`.
+ * Errors: D8_ERR_ARG, or the first error of the runs if every tile failed. */
+d8_status d8_batch_autotune(d8_ctx* ctx, int n, const int64_t* H, const int64_t* W, const float* const* z,
+                            uint8_t* const* dir, uint32_t* const* A, d8_rule rule, d8_stream stream, int* best_tile,
+                            float* ms);
+
 /* Synchronise `stream`, read and clear the context's device status word.
  * Returns D8_OK or the first device-side error recorded (NONFINITE, ARG,
  * CYCLE, TIMEOUT, in that order of precedence). */

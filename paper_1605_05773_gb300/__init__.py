@@ -22,14 +22,14 @@ from . import build as _build
 
 __all__ = [
     "load", "flowdir", "accumulate", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
-    "weighted_upslope", "WeightedUpslope", "BatchPlan", "get_status", "set_tile", "set_profiling",
+    "weighted_upslope", "WeightedUpslope", "BatchPlan", "autotune_batch", "get_status", "set_tile", "set_profiling",
     "stage_times", "D8Error", "OUTLET", "SINK", "RULES",
 ]
 
 OUTLET, SINK = 8, 9
 RULES = {"steepest": 0, "lowest": 1}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_NONFINITE", 4: "ERR_CYCLE", 5: "ERR_NOMEM",
-          6: "ERR_CUDA", 7: "ERR_TIMEOUT"}
+          6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
 
 _lib = None
 _lock = threading.Lock()
@@ -77,6 +77,9 @@ def load() -> ctypes.CDLL:
             "d8_batch_plan": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp)],
             "d8_batch_flowdir_accumulate": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp],
             "d8_batch_destroy": [vp],
+            "d8_batch_autotune": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp),
+                                  ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp, ctypes.POINTER(i32),
+                                  ctypes.POINTER(ctypes.c_float)],
             "d8_get_status": [vp, vp],
             "d8_set_profiling": [vp, i32],
             "d8_stage_times": [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i64), i32, ctypes.POINTER(i32)],
@@ -249,6 +252,42 @@ def check_status(what: str = "device", device=None):
         raise D8Error([k for k, v in STATUS.items() if v == st][0], what)
 
 
+def _batch_buffers(shapes, zs, dirs, As, device):
+    n = len(shapes)
+    if len(zs) != n:
+        raise ValueError("one elevation grid per planned DEM")
+    dirs = dirs or [torch.empty(s, dtype=torch.uint8, device=device) for s in shapes]
+    As = As or [torch.empty(s, dtype=torch.uint32, device=device) for s in shapes]
+    for k, (z, d, a) in enumerate(zip(zs, dirs, As)):
+        for t, dt, nm in ((z, torch.float32, "z"), (d, torch.uint8, "dir"), (a, torch.uint32, "A")):
+            if tuple(t.shape) != shapes[k] or not t.is_contiguous() or t.dtype != dt or not t.is_cuda:
+                raise ValueError(f"{nm}[{k}] must be a contiguous CUDA {dt} tensor of shape {shapes[k]}")
+    vp = ctypes.c_void_p
+    ptrs = tuple((vp * n)(*[t.data_ptr() for t in ts]) for ts in (zs, dirs, As))
+    return dirs, As, ptrs
+
+
+def autotune_batch(zs, dirs=None, As=None, rule: str = "steepest", device=None):
+    """Pick the tile side for a batch by timing the batched pipeline with each
+    (d8_batch_autotune).  Sets the tile for later calls on this device and
+    returns (tile, {tile: ms per run})."""
+    global _tile
+    L = load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    shapes = [tuple(int(x) for x in z.shape) for z in zs]
+    n = len(shapes)
+    dirs, As, (zp, dp, ap) = _batch_buffers(shapes, zs, dirs, As, dev)
+    Hs = (ctypes.c_int64 * n)(*[h for h, _ in shapes])
+    Ws = (ctypes.c_int64 * n)(*[w for _, w in shapes])
+    best = ctypes.c_int()
+    ms = (ctypes.c_float * 3)()
+    _check(L.d8_batch_autotune(context(dev), n, Hs, Ws, zp, dp, ap, RULES[rule],
+                               ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream), ctypes.byref(best), ms),
+           "d8_batch_autotune")
+    _tile = best.value
+    return best.value, {t: float(m) for t, m in zip((32, 64, 128), ms)}
+
+
 class BatchPlan:
     """Many DEMs in one pipeline: persistent launches over all tiles of all
     DEMs with a device tile work queue, replayed from a CUDA graph."""
@@ -264,19 +303,8 @@ class BatchPlan:
         _check(L.d8_batch_plan(context(self.device), n, Hs, Ws, ctypes.byref(self._h)), "d8_batch_plan")
 
     def run(self, zs, dirs=None, As=None, rule: str = "steepest"):
-        n = len(self.shapes)
-        if len(zs) != n:
-            raise ValueError("one elevation grid per planned DEM")
-        dirs = dirs or [torch.empty(s, dtype=torch.uint8, device=self.device) for s in self.shapes]
-        As = As or [torch.empty(s, dtype=torch.uint32, device=self.device) for s in self.shapes]
-        for k, (z, d, a) in enumerate(zip(zs, dirs, As)):
-            for t, dt, nm in ((z, torch.float32, "z"), (d, torch.uint8, "dir"), (a, torch.uint32, "A")):
-                if tuple(t.shape) != self.shapes[k] or not t.is_contiguous() or t.dtype != dt or not t.is_cuda:
-                    raise ValueError(f"{nm}[{k}] must be a contiguous CUDA {dt} tensor of shape {self.shapes[k]}")
+        dirs, As, (zp, dp, ap) = _batch_buffers(self.shapes, zs, dirs, As, self.device)
         vp = ctypes.c_void_p
-        zp = (vp * n)(*[z.data_ptr() for z in zs])
-        dp = (vp * n)(*[d.data_ptr() for d in dirs])
-        ap = (vp * n)(*[a.data_ptr() for a in As])
         _check(load().d8_batch_flowdir_accumulate(self._h, zp, dp, ap, RULES[rule],
                                                   vp(torch.cuda.current_stream(self.device).cuda_stream)),
                "d8_batch_flowdir_accumulate")

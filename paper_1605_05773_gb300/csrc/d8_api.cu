@@ -744,4 +744,61 @@ d8_status d8_batch_destroy(d8_batch* b) {
   return D8_OK;
 }
 
+// Autotuner for batches: the tile side sets how the paper's partitions map
+// onto the GPU (shared memory per tile, tiles per SM, perimeter share, combine
+// depth), and the best one depends on the mix of DEM sizes, so it is measured.
+d8_status d8_batch_autotune(d8_ctx* c, int n, const int64_t* H, const int64_t* W, const float* const* z,
+                            uint8_t* const* dir, uint32_t* const* A, d8_rule rule, d8_stream stream, int* best_tile,
+                            float* ms) {
+  if (!c || !best_tile || n < 1 || !H || !W || !z || !dir || !A || (rule != 0 && rule != 1)) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  static const int kTiles[3] = {32, 64, 128};
+  const int old_T = c->T;
+  int best = -1;
+  float best_ms = 0.0f;
+  d8_status first_err = D8_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return D8_ERR_CUDA;
+  }
+  for (int k = 0; k < 3; k++) {
+    if (ms) ms[k] = -1.0f;
+    c->T = kTiles[k];
+    d8_batch* b = nullptr;
+    d8_status st = d8_batch_plan(c, n, H, W, &b);
+    // one run captures the graph and warms the caches, then two replays are timed
+    if (st == D8_OK) st = d8_batch_flowdir_accumulate(b, z, dir, A, rule, stream);
+    if (st == D8_OK && cudaEventRecord(e0, s) != cudaSuccess) st = D8_ERR_CUDA;
+    for (int r = 0; r < 2 && st == D8_OK; r++) st = d8_batch_flowdir_accumulate(b, z, dir, A, rule, stream);
+    if (st == D8_OK && cudaEventRecord(e1, s) != cudaSuccess) st = D8_ERR_CUDA;
+    if (st == D8_OK && cudaEventSynchronize(e1) != cudaSuccess) st = D8_ERR_CUDA;
+    float t = 0.0f;
+    if (st == D8_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = D8_ERR_CUDA;
+    if (b) d8_batch_destroy(b);
+    if (st != D8_OK) {
+      if (first_err == D8_OK) first_err = st;
+      cudaGetLastError();
+      continue;
+    }
+    t *= 0.5f;
+    if (ms) ms[k] = t;
+    if (best < 0 || t < best_ms) {
+      best = kTiles[k];
+      best_ms = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) {
+    c->T = old_T;
+    return first_err == D8_OK ? D8_ERR_CUDA : first_err;
+  }
+  c->T = best;
+  *best_tile = best;
+  return D8_OK;
+}
+
 }  // extern "C"

@@ -73,7 +73,7 @@ struct WL {
   __device__ static __forceinline__ int code(uint32_t w) { return (int)((w >> CB) & 0xFu); }  // non-IN cells
   __device__ static __forceinline__ int next(uint32_t w, int c) {
     if (IDX) return (int)((w >> CB) & (uint32_t)(T * T - 1));
-    return c + toff_tab<T>(code(w));
+    return c + toff_tab<T>(code(w) & 7);  // (only used for IN cells, codes 0..7)
   }
 };
 

@@ -52,3 +52,29 @@ def test_batch_512_dems(d8):
             np.testing.assert_array_equal(d.cpu().numpy(), d_ref)
             np.testing.assert_array_equal(u32(A), oracle.accumulate(d_ref))
     plan.close()
+
+
+def test_autotune_picks_a_tile_and_keeps_results_exact(d8):
+    """The autotuner times the batch with every tile side, leaves the fastest
+    set, and every candidate produces the oracle's results."""
+    shapes = [(200, 300), (513, 129), (64, 64), (1000, 257), (129, 700)]
+    zs = [demgen.fractal(h, w, seed=300 + k, cache=False) for k, (h, w) in enumerate(shapes)]
+    zt = [to_dev(z) for z in zs]
+    try:
+        tile, ms = d8.autotune_batch(zt)
+        assert tile in (32, 64, 128)
+        assert set(ms) == {32, 64, 128} and all(v > 0 for v in ms.values())
+        assert ms[tile] == min(ms.values())
+        # the last tuning run (tile 128) left its results in the buffers it made;
+        # a plan made now uses the chosen tile
+        plan = d8.BatchPlan(shapes)
+        dirs, As = plan.run(zt)
+        torch.cuda.synchronize()
+        assert d8.get_status() == "OK"
+        for z, d, A in zip(zs, dirs, As):
+            d_ref = oracle.flowdir(z)
+            np.testing.assert_array_equal(d.cpu().numpy(), d_ref)
+            np.testing.assert_array_equal(u32(A), oracle.accumulate(d_ref))
+        plan.close()
+    finally:
+        d8.set_tile(64)
