@@ -184,11 +184,12 @@ HShape hier_shape(int T, int n, const int64_t* H, const int64_t* W) {
   return hs;
 }
 
-size_t hier_bytes(const HShape& hs) {
+// vb: bytes per level value (4 for unit counts, 8 for the weighted doubles)
+size_t hier_bytes(const HShape& hs, size_t vb) {
   size_t b = 0;
   for (int l = 1; l <= hs.nlev; l++) {
     const size_t ns = (size_t)hs.nunits[l] * 4 * hs.S[l];
-    b += align256(ns * 2) + 2 * align256(ns * 4);
+    b += align256(ns * 2) + 2 * align256(ns * vb);
   }
   const size_t nt = (size_t)hs.nunits[hs.nlev] * 4 * hs.S[hs.nlev];
   if (hs.need_top) b += 3 * align256(nt * 4);
@@ -197,9 +198,13 @@ size_t hier_bytes(const HShape& hs) {
 }
 
 // Carve the level arrays; level 0 takes the tile pipeline's arrays.  `dts`
-// holds each level's DEM table (filled by the caller).
-HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dts) {
+// holds each level's DEM table (filled by the caller).  Weighted: the tiles'
+// float-float pval is level 0's input, its double fin lives in the pipe's
+// second value buffer (unused by this combine) and is rounded into Pipe::S.
+HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dts, bool weighted) {
   HPlan hp{};
+  hp.weighted = weighted;
+  hp.ff_out = weighted ? p.S : nullptr;
   hp.nlev = hs.nlev;
   hp.need_top = hs.need_top;
   hp.status = p.status;
@@ -207,8 +212,9 @@ HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dt
   hp.lev[0].nunits = hs.nunits[0];
   hp.lev[0].dt = dts[0];
   hp.lev[0].pex = p.pex;
-  hp.lev[0].pval = static_cast<uint32_t*>(p.pval);
-  hp.lev[0].fin = static_cast<uint32_t*>(p.S);
+  hp.lev[0].pval = p.pval;
+  hp.lev[0].fin = weighted ? p.S2 : p.S;
+  const size_t vb = weighted ? 8 : 4;
   char* q = static_cast<char*>(base);
   for (int l = 1; l <= hs.nlev; l++) {
     const size_t ns = (size_t)hs.nunits[l] * 4 * hs.S[l];
@@ -218,10 +224,10 @@ HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dt
     L.dt = dts[l];
     L.pex = reinterpret_cast<uint16_t*>(q);
     q += align256(ns * 2);
-    L.pval = reinterpret_cast<uint32_t*>(q);
-    q += align256(ns * 4);
-    L.fin = reinterpret_cast<uint32_t*>(q);
-    q += align256(ns * 4);
+    L.pval = q;
+    q += align256(ns * vb);
+    L.fin = q;
+    q += align256(ns * vb);
   }
   const size_t nt = (size_t)hs.nunits[hs.nlev] * 4 * hs.S[hs.nlev];
   if (hs.need_top) {
@@ -285,12 +291,8 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   const bool weighted = (mode == UP_WEIGHTED);
   const size_t vb = weighted ? 8 : 4;
   if (up_smem_bytes(T, mode) == 0 || down_smem_bytes(T, weighted) == 0) return D8_ERR_ARG;
-  HShape hs;
-  size_t hb = 0;
-  if (!weighted) {
-    hs = hier_shape(T, 1, &d.H, &d.W);
-    hb = hier_bytes(hs);
-  }
+  const HShape hs = hier_shape(T, 1, &d.H, &d.W);
+  const size_t hb = hier_bytes(hs, vb);
   const size_t pb = align256(pipe_bytes(ntiles, T, vb));
   d8_status st = ensure_ws(c, pb + hb);
   if (st != D8_OK) return st;
@@ -311,20 +313,16 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   if (e != cudaSuccess) return cuda_fail(e);
   {
     StageScope sc(c, ST_COMBINE, s);
-    if (weighted) {
-      e = launch_combine_fwd(dt, p, weighted, s, &sc.n);
-    } else {
-      DemTable dts[HMAX + 1];
-      for (int l = 0; l <= hs.nlev; l++) {
-        DemDesc dl = d;
-        dl.ntx = (d.W + hs.S[l] - 1) / hs.S[l];
-        dl.nty = (d.H + hs.S[l] - 1) / hs.S[l];
-        dl.tile_base = 0;
-        dts[l] = single(dl);
-      }
-      const HPlan hp = carve_hier(static_cast<char*>(c->ws) + pb, hs, p, dts);
-      e = launch_combine_hier(hp, s, &sc.n);
+    DemTable dts[HMAX + 1];
+    for (int l = 0; l <= hs.nlev; l++) {
+      DemDesc dl = d;
+      dl.ntx = (d.W + hs.S[l] - 1) / hs.S[l];
+      dl.nty = (d.H + hs.S[l] - 1) / hs.S[l];
+      dl.tile_base = 0;
+      dts[l] = single(dl);
     }
+    const HPlan hp = carve_hier(static_cast<char*>(c->ws) + pb, hs, p, dts, weighted);
+    e = launch_combine_hier(hp, s, &sc.n);
   }
   if (e != cudaSuccess) return cuda_fail(e);
   {
@@ -589,7 +587,7 @@ d8_status d8_batch_plan(d8_ctx* c, int n, const int64_t* H, const int64_t* W, d8
     b->lev_units[l] = hs.nunits[l];
   }
   b->pipe_part = align256(pipe_bytes(base, b->T, 4));
-  b->ws_bytes = b->pipe_part + hier_bytes(hs);
+  b->ws_bytes = b->pipe_part + hier_bytes(hs, 4);
   for (int l = 1; l <= hs.nlev; l++) {
     std::vector<int32_t> map((size_t)hs.nunits[l]);
     b->lev_host[l].resize(n);
@@ -651,7 +649,7 @@ static cudaError_t batch_enqueue(d8_batch* b, int rule, cudaStream_t s, int* n_u
     if (b->n == 1) t.ndem = 1;
     dts[l] = t;
   }
-  const HPlan hp = carve_hier(static_cast<char*>(b->ws) + b->pipe_part, hs, p, dts);
+  const HPlan hp = carve_hier(static_cast<char*>(b->ws) + b->pipe_part, hs, p, dts, false);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
   if (e == cudaSuccess) e = launch_up(dt, p, UP_UNIT_Z, rule, s, n_up);
   if (e == cudaSuccess) e = launch_combine_hier(hp, s, n_comb);

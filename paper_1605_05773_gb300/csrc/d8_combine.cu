@@ -16,6 +16,12 @@
 // its child exits and the same walks give every child exit its final area;
 // at level 0 that is the final area of every tile exit, which the tiles'
 // finalising pass reads.
+//
+// Unit counts travel as uint32.  Weighted areas travel as doubles above the
+// tiles (shared-memory and global fp64 atomic adds; the level sums carry more
+// precision than the tiles' float-float values they start from), and the
+// level-0 results are rounded back to float-float (hi = fp32 nearest, lo =
+// fp32 nearest of the remainder) for the finalising pass.
 #include "d8_device.cuh"
 
 namespace d8 {
@@ -28,19 +34,24 @@ constexpr uint16_t N_ROOT = 0xFFFFu;  // path ends inside the group
 constexpr uint16_t N_OUT = 0xFFFEu;   // parent lies outside the group (a group exit)
 constexpr uint16_t N_NONE = 0xFFFDu;  // not an exit slot
 
-template <int S, int G>
+template <int S, int G, class V>
 struct GroupLayout {
   static constexpr int NS = G * G * 4 * S;  // child slots of a group
   static constexpr size_t off_spx = 0;                      // u16 child exit codes
   static constexpr size_t off_par = off_spx + (size_t)NS * 2;  // u16 parent node
-  static constexpr size_t off_val = off_par + (size_t)NS * 2;  // u32 value
-  static constexpr size_t off_deg = off_val + (size_t)NS * 4;  // u32 unfinished children
+  static constexpr size_t off_val = (off_par + (size_t)NS * 2 + 15) / 16 * 16;  // value
+  static constexpr size_t off_deg = off_val + (size_t)NS * sizeof(V);  // u32 unfinished children
   static constexpr size_t off_src = off_deg + (size_t)NS * 4;  // u16 source lists
   static constexpr size_t off_misc = off_src + (size_t)NS * 2;
   static constexpr size_t bytes = off_misc + 64;
 };
 
 __device__ __forceinline__ DemDesc dem_by_index(const DemTable& t, int k) { return t.ndem == 1 ? t.one : t.table[k]; }
+
+// a child's stored value in the accumulation type (float-float -> double is exact)
+__device__ __forceinline__ uint32_t to_acc(uint32_t v, uint32_t) { return v; }
+__device__ __forceinline__ double to_acc(double v, double) { return v; }
+__device__ __forceinline__ double to_acc(ff v, double) { return (double)v.hi + (double)v.lo; }
 
 struct UnitGeo {
   int64_t i0, j0;
@@ -59,21 +70,21 @@ __device__ __forceinline__ UnitGeo unit_geo(const DemDesc& d, int64_t uy, int64_
 // Load the children of group (gy, gx) and compute every child exit's parent
 // inside the group and the children count of every node.
 // Returns the number of child exits this thread loaded.
-template <int S, int G>
-__device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint16_t* cpex, const uint32_t* cpval,
-                          uint16_t* spx, uint16_t* par, uint32_t* val, uint32_t* deg) {
+template <int S, int G, class V, class CV>
+__device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint16_t* cpex, const CV* cpval,
+                          uint16_t* spx, uint16_t* par, V* val, uint32_t* deg) {
   constexpr int NS = G * G * 4 * S;
   int exits = 0;
   for (int n = threadIdx.x; n < NS; n += NTG) {
     const int lt = n / (4 * S), s = n - lt * (4 * S);
     const int64_t cy = gy * G + lt / G, cx = gx * G + lt % G;
     uint16_t pe = PEX_TERM;
-    uint32_t v = 0;
+    V v = 0;
     if (cy < cd.nty && cx < cd.ntx) {
       const int64_t cu = cd.tile_base + cy * cd.ntx + cx;
       pe = cpex[cu * (4 * S) + s];
       if (pe & PEX_EXIT) {
-        v = cpval[cu * (4 * S) + s];
+        v = to_acc(cpval[cu * (4 * S) + s], V());
         exits++;
       }
     }
@@ -122,8 +133,8 @@ __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint1
 // parent, then (after a block fence) decrements the parent's children count;
 // the last child continues at the parent (after a fence, so it sees every
 // child's addition).  Returns the number of nodes this thread finished.
-template <int S, int G>
-__device__ int group_walk(uint16_t* spx, const uint16_t* par, uint32_t* val, uint32_t* deg, uint16_t* srcl) {
+template <int S, int G, class V>
+__device__ int group_walk(uint16_t* spx, const uint16_t* par, V* val, uint32_t* deg, uint16_t* srcl) {
   constexpr int NS = G * G * 4 * S;
   constexpr int NW = NTG / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -138,7 +149,7 @@ __device__ int group_walk(uint16_t* spx, const uint16_t* par, uint32_t* val, uin
   }
   __syncthreads();
   int done = 0, head = 0, cur = -1;
-  uint32_t v = 0;
+  V v = 0;
   const unsigned lt = (1u << lane) - 1u;
   for (;;) {
     if (head < n) {
@@ -165,7 +176,7 @@ __device__ int group_walk(uint16_t* spx, const uint16_t* par, uint32_t* val, uin
       if (old == 1u) {
         __threadfence_block();
         cur = p;
-        v = *(volatile uint32_t*)&val[p];
+        v = *(volatile V*)&val[p];
         done++;
       } else {
         cur = -1;
@@ -175,15 +186,15 @@ __device__ int group_walk(uint16_t* spx, const uint16_t* par, uint32_t* val, uin
   return done;
 }
 
-template <int S, int G>
-__global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, const uint16_t* cpex,
-                                                    const uint32_t* cpval, uint16_t* gpex, uint32_t* gpval,
-                                                    int64_t ngroups, uint32_t* queue, uint32_t* status) {
-  using L = GroupLayout<S, G>;
+template <int S, int G, class V, class CV>
+__global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, const uint16_t* cpex, const CV* cpval,
+                                                    uint16_t* gpex, V* gpval, int64_t ngroups, uint32_t* queue,
+                                                    uint32_t* status) {
+  using L = GroupLayout<S, G, V>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint16_t* spx = reinterpret_cast<uint16_t*>(sm + L::off_spx);
   uint16_t* par = reinterpret_cast<uint16_t*>(sm + L::off_par);
-  uint32_t* val = reinterpret_cast<uint32_t*>(sm + L::off_val);
+  V* val = reinterpret_cast<V*>(sm + L::off_val);
   uint32_t* deg = reinterpret_cast<uint32_t*>(sm + L::off_deg);
   uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
@@ -199,8 +210,8 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
       misc[0] = 0;
       misc[1] = 0;
     }
-    const int exits = group_load<S, G>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
-    const int done = group_walk<S, G>(spx, par, val, deg, srcl);
+    const int exits = group_load<S, G, V, CV>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
+    const int done = group_walk<S, G, V>(spx, par, val, deg, srcl);
     atomicAdd(&misc[0], done);
     atomicAdd(&misc[1], exits);
     __syncthreads();
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
     for (int gs = threadIdx.x; gs < 4 * GS; gs += NTG) {
       int ci, cj;
       uint16_t gpe = PEX_TERM;
-      uint32_t gv = 0;
+      V gv = 0;
       if (slot_cell(gs, gg.h, gg.w, GS, ci, cj)) {
         const int a = ci / S, b = cj / S;
         const UnitGeo cu = unit_geo(cd, gy * G + a, gx * G + b, S);
@@ -247,15 +258,14 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
   }
 }
 
-template <int S, int G>
-__global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, const uint16_t* cpex,
-                                                      const uint32_t* cpval, uint32_t* cfin, const uint32_t* gfin,
-                                                      int64_t ngroups, uint32_t* queue) {
-  using L = GroupLayout<S, G>;
+template <int S, int G, class V, class CV>
+__global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, const uint16_t* cpex, const CV* cpval,
+                                                      V* cfin, const V* gfin, int64_t ngroups, uint32_t* queue) {
+  using L = GroupLayout<S, G, V>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint16_t* spx = reinterpret_cast<uint16_t*>(sm + L::off_spx);
   uint16_t* par = reinterpret_cast<uint16_t*>(sm + L::off_par);
-  uint32_t* val = reinterpret_cast<uint32_t*>(sm + L::off_val);
+  V* val = reinterpret_cast<V*>(sm + L::off_val);
   uint32_t* deg = reinterpret_cast<uint32_t*>(sm + L::off_deg);
   uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
   constexpr int NS = L::NS;
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
     const DemDesc cd = dem_by_index(cdt, dem);
     const int64_t lg = gu - gd.tile_base;
     const int64_t gy = lg / gd.ntx, gx = lg % gd.ntx;
-    group_load<S, G>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
+    group_load<S, G, V, CV>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
     // inflow across the group border: each border cell r receives the final
     // areas of the outside cells draining into it; the inflow then follows
     // r's path inside its child unit to that child's exit
@@ -275,7 +285,8 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
       int ci, cj;
       if (!slot_cell(gs, gg.h, gg.w, GS, ci, cj)) continue;
       const int64_t gi = gg.i0 + ci, gj = gg.j0 + cj;
-      uint32_t in = 0;
+      V in = 0;
+      bool any = false;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         const int li = ci + code_di(k), lj = cj + code_dj(k);
@@ -284,8 +295,9 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
         if (ni < 0 || nj < 0 || ni >= gd.H || nj >= gd.W) continue;
         if (gd.dir[ni * gd.lddir + nj] != opposite(k)) continue;
         in += gfin[global_slot(gd, ni, nj, GS)];
+        any = true;
       }
-      if (!in) continue;
+      if (!any) continue;
       const int a = ci / S, b = cj / S;
       const UnitGeo cu = unit_geo(cd, gy * G + a, gx * G + b, S);
       const int lt = a * G + b;
@@ -297,7 +309,7 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
         atomicAdd(&val[lt * (4 * S) + pe], in);
     }
     __syncthreads();
-    group_walk<S, G>(spx, par, val, deg, srcl);
+    group_walk<S, G, V>(spx, par, val, deg, srcl);
     __syncthreads();
     for (int n = threadIdx.x; n < NS; n += NTG) {
       if (!(spx[n] & PEX_EXIT)) continue;
@@ -310,9 +322,9 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
 
 // ---- top level: Algorithms 5-6 over the remaining units, in global memory
 
-template <int S>
-__global__ void k_top_init(DemTable dt, const uint16_t* pex, const uint32_t* pval, uint32_t* fin, uint32_t* par,
-                           uint32_t* deg, int64_t nslots) {
+template <int S, class V, class CV>
+__global__ void k_top_init(DemTable dt, const uint16_t* pex, const CV* pval, V* fin, uint32_t* par, uint32_t* deg,
+                           int64_t nslots) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
     const uint16_t pe = pex[g];
@@ -333,7 +345,7 @@ __global__ void k_top_init(DemTable dt, const uint16_t* pex, const uint32_t* pva
       else if (pey != PEX_TERM)
         pr = (uint32_t)((y / (4 * S)) * (4 * S) + pey);
       if (pr != ROOT) atomicAdd(&deg[pr], 1u);
-      fin[g] = pval[g];
+      fin[g] = to_acc(pval[g], V());
     }
     par[g] = pr;
   }
@@ -349,13 +361,13 @@ __global__ void k_top_sources(const uint16_t* pex, const uint32_t* deg, uint32_t
 }
 
 // Algorithm 6 with global atomics: last-arriver walks up the exit forest.
-__global__ void k_top_walk(const uint32_t* par, uint32_t* fin, uint32_t* deg, const uint32_t* list,
-                           uint32_t* counters) {
+template <class V>
+__global__ void k_top_walk(const uint32_t* par, V* fin, uint32_t* deg, const uint32_t* list, uint32_t* counters) {
   const uint32_t n = *(volatile const uint32_t*)&counters[0];
   uint32_t done = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t x = list[i];
-    uint32_t v = fin[x];
+    V v = fin[x];
     done++;
     for (;;) {
       const uint32_t p = par[x];
@@ -365,57 +377,70 @@ __global__ void k_top_walk(const uint32_t* par, uint32_t* fin, uint32_t* deg, co
       if (atomicSub(&deg[p], 1u) != 1u) break;
       __threadfence();
       x = p;
-      v = *(volatile uint32_t*)&fin[p];
+      v = *(volatile V*)&fin[p];
       done++;
     }
   }
   if (done) atomicAdd(&counters[2], done);
 }
 
+// weighted: level-0 final values at exits, double -> float-float
+__global__ void k_round_ff(const uint16_t* pex, const double* fin, ff* out, int64_t nslots) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
+    if (!(pex[g] & PEX_EXIT)) continue;
+    const double v = fin[g];
+    const float hi = __double2float_rn(v);
+    out[g] = ff{hi, __double2float_rn(v - (double)hi)};
+  }
+}
+
 __global__ void k_top_check(const uint32_t* counters, uint32_t* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && counters[1] != counters[2]) set_status(status, D8_ERR_CYCLE);
 }
 
-template <int S, int G>
-static cudaError_t launch_level_up(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex,
-                                   const uint32_t* cpval, uint16_t* gpex, uint32_t* gpval, int64_t ngroups,
-                                   uint32_t* queue, uint32_t* status, cudaStream_t s) {
-  using L = GroupLayout<S, G>;
-  cudaError_t e = cudaFuncSetAttribute(k_group_up<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+template <int S, int G, class V, class CV>
+static cudaError_t launch_level_up(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex, const void* cpval,
+                                   uint16_t* gpex, void* gpval, int64_t ngroups, uint32_t* queue, uint32_t* status,
+                                   cudaStream_t s) {
+  using L = GroupLayout<S, G, V>;
+  auto k = k_group_up<S, G, V, CV>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 1, dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_up<S, G>, NTG, L::bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NTG, L::bytes);
   int64_t grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * sms;
   if (grid > ngroups) grid = ngroups;
   e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  k_group_up<S, G><<<(unsigned)grid, NTG, L::bytes, s>>>(cdt, gdt, cpex, cpval, gpex, gpval, ngroups, queue, status);
+  k<<<(unsigned)grid, NTG, L::bytes, s>>>(cdt, gdt, cpex, static_cast<const CV*>(cpval), gpex, static_cast<V*>(gpval),
+                                          ngroups, queue, status);
   return cudaGetLastError();
 }
 
-template <int S, int G>
-static cudaError_t launch_level_down(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex,
-                                     const uint32_t* cpval, uint32_t* cfin, const uint32_t* gfin, int64_t ngroups,
-                                     uint32_t* queue, cudaStream_t s) {
-  using L = GroupLayout<S, G>;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_group_down<S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+template <int S, int G, class V, class CV>
+static cudaError_t launch_level_down(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex, const void* cpval,
+                                     void* cfin, const void* gfin, int64_t ngroups, uint32_t* queue, cudaStream_t s) {
+  using L = GroupLayout<S, G, V>;
+  auto k = k_group_down<S, G, V, CV>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 1, dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_down<S, G>, NTG, L::bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NTG, L::bytes);
   int64_t grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * sms;
   if (grid > ngroups) grid = ngroups;
   e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  k_group_down<S, G><<<(unsigned)grid, NTG, L::bytes, s>>>(cdt, gdt, cpex, cpval, cfin, gfin, ngroups, queue);
+  k<<<(unsigned)grid, NTG, L::bytes, s>>>(cdt, gdt, cpex, static_cast<const CV*>(cpval), static_cast<V*>(cfin),
+                                          static_cast<const V*>(gfin), ngroups, queue);
   return cudaGetLastError();
 }
 
-template <int S>
+template <int S, class V, class CV>
 static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& top, cudaStream_t s, int* nl) {
   const int64_t ns = lv.nunits * 4 * S;
   cudaError_t e = cudaMemsetAsync(top.deg, 0, sizeof(uint32_t) * (size_t)ns, s);
@@ -427,9 +452,11 @@ static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& 
   int64_t b = (ns + 255) / 256;
   if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
   if (b < 1) b = 1;
-  k_top_init<S><<<(unsigned)b, 256, 0, s>>>(dt, lv.pex, lv.pval, lv.fin, top.par, top.deg, ns);
+  k_top_init<S, V, CV><<<(unsigned)b, 256, 0, s>>>(dt, lv.pex, static_cast<const CV*>(lv.pval),
+                                                   static_cast<V*>(lv.fin), top.par, top.deg, ns);
   k_top_sources<<<(unsigned)b, 256, 0, s>>>(lv.pex, top.deg, top.list, top.counters, ns);
-  k_top_walk<<<(unsigned)(sms * 8), 256, 0, s>>>(top.par, lv.fin, top.deg, top.list, top.counters);
+  k_top_walk<V><<<(unsigned)(sms * 8), 256, 0, s>>>(top.par, static_cast<V*>(lv.fin), top.deg, top.list,
+                                                    top.counters);
   k_top_check<<<1, 32, 0, s>>>(top.counters, top.status);
   *nl += 4;
   return cudaGetLastError();
@@ -452,18 +479,25 @@ int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels) {
   return n;
 }
 
-cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch) {
+namespace cmb {
+
+// V: accumulation type above the tiles; CV0: the tiles' stored pval type
+template <class V, class CV0>
+static cudaError_t combine_hier_t(const HPlan& hp, cudaStream_t s, int* nlaunch) {
   cudaError_t e = cudaSuccess;
   // up: level l-1 -> l
   for (int l = 1; l <= hp.nlev && e == cudaSuccess; l++) {
     const HLevel& c = hp.lev[l - 1];
     const HLevel& g = hp.lev[l];
     const int S = c.S, G = g.S / c.S;
-#define D8_UP(SS, GG)                                                                                            \
-  if (S == SS && G == GG) {                                                                                     \
-    e = cmb::launch_level_up<SS, GG>(c.dt, g.dt, c.pex, c.pval, g.pex, g.pval, g.nunits, hp.queue + l, hp.status, s); \
-    ++*nlaunch;                                                                                                 \
-    continue;                                                                                                   \
+#define D8_UP(SS, GG)                                                                                             \
+  if (S == SS && G == GG) {                                                                                      \
+    e = l == 1 ? launch_level_up<SS, GG, V, CV0>(c.dt, g.dt, c.pex, c.pval, g.pex, g.pval, g.nunits, hp.queue + l,  \
+                                                 hp.status, s)                                                   \
+               : launch_level_up<SS, GG, V, V>(c.dt, g.dt, c.pex, c.pval, g.pex, g.pval, g.nunits, hp.queue + l,    \
+                                               hp.status, s);                                                    \
+    ++*nlaunch;                                                                                                  \
+    continue;                                                                                                    \
   }
     D8_UP(32, 4) D8_UP(64, 4) D8_UP(128, 2) D8_UP(256, 2) D8_UP(512, 2)
 #undef D8_UP
@@ -473,15 +507,16 @@ cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch) {
   // top
   const HLevel& t = hp.lev[hp.nlev];
   if (hp.need_top) {
+    const bool l0 = hp.nlev == 0;
+#define D8_TOP(SS)                                                                                 \
+  case SS:                                                                                         \
+    e = l0 ? launch_top<SS, V, CV0>(t.dt, t, hp.top, s, nlaunch) : launch_top<SS, V, V>(t.dt, t, hp.top, s, nlaunch); \
+    break;
     switch (t.S) {
-      case 32: e = cmb::launch_top<32>(t.dt, t, hp.top, s, nlaunch); break;
-      case 64: e = cmb::launch_top<64>(t.dt, t, hp.top, s, nlaunch); break;
-      case 128: e = cmb::launch_top<128>(t.dt, t, hp.top, s, nlaunch); break;
-      case 256: e = cmb::launch_top<256>(t.dt, t, hp.top, s, nlaunch); break;
-      case 512: e = cmb::launch_top<512>(t.dt, t, hp.top, s, nlaunch); break;
-      case 1024: e = cmb::launch_top<1024>(t.dt, t, hp.top, s, nlaunch); break;
+      D8_TOP(32) D8_TOP(64) D8_TOP(128) D8_TOP(256) D8_TOP(512) D8_TOP(1024)
       default: return cudaErrorInvalidValue;
     }
+#undef D8_TOP
     if (e != cudaSuccess) return e;
   }
   // down: level l -> l-1
@@ -489,17 +524,39 @@ cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch) {
     const HLevel& c = hp.lev[l - 1];
     const HLevel& g = hp.lev[l];
     const int S = c.S, G = g.S / c.S;
-#define D8_DN(SS, GG)                                                                                                \
-  if (S == SS && G == GG) {                                                                                         \
-    e = cmb::launch_level_down<SS, GG>(c.dt, g.dt, c.pex, c.pval, c.fin, g.fin, g.nunits, hp.queue + 16 + l, s); \
-    ++*nlaunch;                                                                                                     \
-    continue;                                                                                                       \
+#define D8_DN(SS, GG)                                                                                               \
+  if (S == SS && G == GG) {                                                                                        \
+    e = l == 1 ? launch_level_down<SS, GG, V, CV0>(c.dt, g.dt, c.pex, c.pval, c.fin, g.fin, g.nunits,               \
+                                                   hp.queue + 16 + l, s)                                           \
+               : launch_level_down<SS, GG, V, V>(c.dt, g.dt, c.pex, c.pval, c.fin, g.fin, g.nunits, hp.queue + 16 + l, \
+                                                 s);                                                               \
+    ++*nlaunch;                                                                                                    \
+    continue;                                                                                                      \
   }
     D8_DN(32, 4) D8_DN(64, 4) D8_DN(128, 2) D8_DN(256, 2) D8_DN(512, 2)
 #undef D8_DN
     return cudaErrorInvalidValue;
   }
   return e;
+}
+
+}  // namespace cmb
+
+cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch) {
+  if (!hp.weighted) return cmb::combine_hier_t<uint32_t, uint32_t>(hp, s, nlaunch);
+  cudaError_t e = cmb::combine_hier_t<double, ff>(hp, s, nlaunch);
+  if (e != cudaSuccess) return e;
+  const HLevel& l0 = hp.lev[0];
+  const int64_t ns = l0.nunits * 4 * l0.S;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (ns + 255) / 256;
+  if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
+  cmb::k_round_ff<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(l0.pex, static_cast<const double*>(l0.fin),
+                                                            static_cast<ff*>(hp.ff_out), ns);
+  ++*nlaunch;
+  return cudaGetLastError();
 }
 
 }  // namespace d8

@@ -72,15 +72,19 @@ cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, i
 // Level 0 units are the tiles; a level-l unit is a G x G block of level-(l-1)
 // units.  Every level has per-unit perimeter summaries of the same format:
 // per perimeter slot the exit code (pex), the in-unit value at exits (pval)
-// and, after the down sweep, the final value at exits (fin).
+// and, after the down sweep, the final value at exits (fin).  Values are
+// uint32 counts (unit weights) or, for weighted areas, doubles on every level
+// except the tiles' own pval (float-float, from the weighted tile pass); the
+// level-0 fin of a weighted run is a double array rounded to float-float for
+// the finalising pass at the end.
 constexpr int HMAX = 8;
 struct HLevel {
   int S;            // unit side in cells
   int64_t nunits;   // units over all DEMs
   DemTable dt;      // per-DEM unit grid (ntx, nty, tile_base) at this level
   uint16_t* pex;
-  uint32_t* pval;
-  uint32_t* fin;
+  void* pval;       // uint32 / double (level 0 weighted: ff)
+  void* fin;        // uint32 / double
 };
 struct HTop {  // the top level's queue-method solve in global memory
   uint32_t* par;
@@ -90,6 +94,8 @@ struct HTop {  // the top level's queue-method solve in global memory
   uint32_t* status;
 };
 struct HPlan {
+  bool weighted;  // double values above the tiles; level-0 fin rounded into ff_out
+  void* ff_out;   // weighted: the tiles' float-float final values at exits (Pipe::S)
   int nlev;  // group levels 1..nlev above the tiles
   HLevel lev[HMAX];
   bool need_top;
