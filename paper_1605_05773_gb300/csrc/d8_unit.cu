@@ -38,6 +38,7 @@ constexpr int NTU = 128;  // threads per tile block (4 warps)
 constexpr int NWU = NTU / 32;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int RING = 64;  // pending sources per warp (a power of two > 63)
+constexpr int NTF = 256;  // threads per finalising block (its walks are few; the loads want warps)
 
 // In-tile offset of direction k (N, NE, E, SE, S, SW, W, NW) for row stride T.
 // For T <= 64 the eight offsets fit in signed bytes of one 64-bit constant
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
 // The work is the summed length of the receivers' in-tile paths (at most
 // 4T * T^2 for adversarial fields, about the sub-forest size on terrain).
 template <int T>
-__global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
+__global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
   using L = FinLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint32_t* F = reinterpret_cast<uint32_t*>(sm + L::off_f);
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
 
   // F[] starts at zero; every tile leaves it at zero again (the output pass
   // clears the words the walks touched)
-  for (int c = threadIdx.x; c < TT / 4; c += NTU) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
+  for (int c = threadIdx.x; c < TT / 4; c += NTF) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) misc[0] = 0;
 
   for (int64_t t = next_tile(p.queue + 1); t < p.ntiles; t = next_tile(p.queue + 1)) {
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
     // the tile's codes (cells outside a ragged tile are never reached)
     {
       const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
-      for (int q = threadIdx.x; q < TT / 4; q += NTU) {
+      for (int q = threadIdx.x; q < TT / 4; q += NTF) {
         const int c = q * 4, i = c / T, j = c - i * T;
         if (i >= g.th) continue;
         const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
       }
     }
     // Algorithm 7: the receivers and their resolved inflow, listed
-    for (int s = threadIdx.x; s < 4 * T; s += NTU) {
+    for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
       uint32_t in = 0;
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
     // Algorithm 8 on the receivers' paths (a path inside one tile has at most
     // T^2 cells; the bound only matters for a field with a cycle, which the
     // first pass reports)
-    for (int r = threadIdx.x; r < nrec; r += NTU) {
+    for (int r = threadIdx.x; r < nrec; r += NTF) {
       const uint32_t in = rin[r];
       int c = rcell[r], i = c / T, j = c & (T - 1);
       atomicAdd(&F[c], in);
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
     __syncthreads();
     if (threadIdx.x == 0) misc[0] = 0;
     // A += F where F is nonzero; touched words go back to zero
-    for (int q = threadIdx.x; q < TT / 4; q += NTU) {
+    for (int q = threadIdx.x; q < TT / 4; q += NTF) {
       const uint4 f = reinterpret_cast<const uint4*>(F)[q];
       if (!(f.x | f.y | f.z | f.w)) continue;
       reinterpret_cast<uint4*>(F)[q] = make_uint4(0, 0, 0, 0);
@@ -448,11 +449,11 @@ __global__ void __launch_bounds__(NTU) k_fin_unit(DemTable dt, Pipe p) {
 }
 
 template <class K>
-static unsigned persistent_grid_u(K kernel, size_t smem, int64_t ntiles) {
+static unsigned persistent_grid_u(K kernel, int threads, size_t smem, int64_t ntiles) {
   int dev = 0, sms = 1, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NTU, smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -466,7 +467,7 @@ static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, cudaStrea
   const size_t bytes = UpLayout<T>::bytes;
   cudaError_t e = cudaFuncSetAttribute(k_up_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_up_unit<T><<<persistent_grid_u(k_up_unit<T>, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
+  k_up_unit<T><<<persistent_grid_u(k_up_unit<T>, NTU, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
@@ -475,7 +476,7 @@ static cudaError_t launch_down_unit_t(const DemTable& dt, const Pipe& p, cudaStr
   const size_t bytes = FinLayout<T>::bytes;
   cudaError_t e = cudaFuncSetAttribute(k_fin_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_fin_unit<T><<<persistent_grid_u(k_fin_unit<T>, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
+  k_fin_unit<T><<<persistent_grid_u(k_fin_unit<T>, NTF, bytes, p.ntiles), NTF, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
