@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(NT) k_bwd_up(DemTable dt, Pipe p) {
   const uint8_t* cl = sm + L::off_cl;
   ff* pval = static_cast<ff*>(p.pval);
   constexpr int TT = T * T;
-  for (int64_t t = next_tile(p.queue + 2); t < p.ntiles; t = next_tile(p.queue + 2)) {
+  TileQueue tq(p.queue + 2, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     const int b = tile_path_sums<T>(d, g, sm, p.status);
@@ -205,7 +206,8 @@ __global__ void __launch_bounds__(NT) k_bwd_down(DemTable dt, Pipe p) {
   const uint32_t last = *(volatile uint32_t*)&p.flags[MAX_ROUNDS + 1];
   const ff* H = static_cast<const ff*>((last & 1) ? p.S2 : p.S);
   constexpr int TT = T * T;
-  for (int64_t t = next_tile(p.queue + 3); t < p.ntiles; t = next_tile(p.queue + 3)) {
+  TileQueue tq(p.queue + 3, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     const int b = tile_path_sums<T>(d, g, sm, p.status);

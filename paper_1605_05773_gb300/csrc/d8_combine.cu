@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
   constexpr int NS = L::NS;
   constexpr int GS = G * S;
-  for (int64_t gu = next_tile(queue); gu < ngroups; gu = next_tile(queue)) {
+  TileQueue tq(queue, ngroups);
+  for (int64_t gu = tq.first(); gu < ngroups; gu = tq.next()) {
     const DemDesc gd = dem_of(gdt, gu);
     const int dem = gdt.ndem == 1 ? 0 : gdt.tile_dem[gu];
     const DemDesc cd = dem_by_index(cdt, dem);
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
       gpex[gu * (4 * GS) + gs] = gpe;
       gpval[gu * (4 * GS) + gs] = gv;
     }
-    // (next_tile's barrier protects shared memory before the next group)
+    // (the queue's barrier protects shared memory before the next group)
   }
 }
 
@@ -270,7 +271,8 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
   uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
   constexpr int NS = L::NS;
   constexpr int GS = G * S;
-  for (int64_t gu = next_tile(queue); gu < ngroups; gu = next_tile(queue)) {
+  TileQueue tq(queue, ngroups);
+  for (int64_t gu = tq.first(); gu < ngroups; gu = tq.next()) {
     const DemDesc gd = dem_of(gdt, gu);
     const int dem = gdt.ndem == 1 ? 0 : gdt.tile_dem[gu];
     const DemDesc cd = dem_by_index(cdt, dem);

@@ -181,14 +181,35 @@ __device__ __forceinline__ uint8_t classify(int code, int i, int j, const TileGe
 
 __device__ __forceinline__ void set_status(uint32_t* status, int code) { atomicOr(status, 1u << code); }
 
-// Tile work queue: persistent blocks take the next tile index from a device
-// counter (zeroed before the launch) until the tiles run out.
-__device__ __forceinline__ int64_t next_tile(uint32_t* queue) {
-  __shared__ int64_t sh_tile;
-  __syncthreads();
-  if (threadIdx.x == 0) sh_tile = (int64_t)atomicAdd(queue, 1u);
-  __syncthreads();
-  return sh_tile;
-}
+// Tile work queue: persistent blocks take tile indices until the n tiles run
+// out.  Block b starts with tile b; later indices come from a device counter
+// (zeroed before the launch) offset by the grid size.  With plenty of tiles
+// per block (more than 4), thread 0 fetches one index ahead: the atomic for
+// the next tile is issued when the current one is handed out and consumed at
+// the next call, so its round trip to L2 overlaps the current tile's work.
+// With few tiles per block a fetched-ahead index would sit reserved behind a
+// busy block, so then each index is fetched when it is needed.
+struct TileQueue {
+  uint32_t* q;
+  bool look;
+  uint32_t ahead = 0;  // thread 0: the index fetched for the next call
+  __device__ TileQueue(uint32_t* queue, int64_t n) : q(queue), look(n > 4 * (int64_t)gridDim.x) {}
+  __device__ __forceinline__ int64_t first() {
+    __syncthreads();
+    if (look && threadIdx.x == 0) ahead = gridDim.x + atomicAdd(q, 1u);
+    return blockIdx.x;
+  }
+  __device__ __forceinline__ int64_t next() {
+    __shared__ int64_t sh_tile;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t now = look ? ahead : gridDim.x + atomicAdd(q, 1u);
+      if (look) ahead = gridDim.x + atomicAdd(q, 1u);
+      sh_tile = (int64_t)now;
+    }
+    __syncthreads();
+    return sh_tile;
+  }
+};
 
 }  // namespace d8

@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(NT) k_up(DemTable dt, Pipe p) {
   uint32_t* misc = reinterpret_cast<uint32_t*>(sm + L::off_misc);
   V* pval = static_cast<V*>(p.pval);
 
-  for (int64_t t = next_tile(p.queue + 0); t < p.ntiles; t = next_tile(p.queue + 0)) {
+  TileQueue tq(p.queue + 0, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     if (threadIdx.x == 0) misc[0] = 0;
@@ -312,7 +313,8 @@ __global__ void __launch_bounds__(NT) k_down(DemTable dt, Pipe p) {
   uint8_t* cl = sm + L::off_cl;
   const V* xval = static_cast<const V*>(p.S);
 
-  for (int64_t t = next_tile(p.queue + 1); t < p.ntiles; t = next_tile(p.queue + 1)) {
+  TileQueue tq(p.queue + 1, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     for (int c = threadIdx.x; c < T * T; c += NT) {

@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
 
-  for (int64_t t = next_tile(p.queue + 0); t < p.ntiles; t = next_tile(p.queue + 0)) {
+  TileQueue tq(p.queue + 0, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     uint4* w4 = reinterpret_cast<uint4*>(word);
@@ -361,7 +362,8 @@ __global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
   for (int c = threadIdx.x; c < TT / 4; c += NTF) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) misc[0] = 0;
 
-  for (int64_t t = next_tile(p.queue + 1); t < p.ntiles; t = next_tile(p.queue + 1)) {
+  TileQueue tq(p.queue + 1, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     // the tile's codes (cells outside a ragged tile are never reached)
