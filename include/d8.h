@@ -104,8 +104,10 @@ d8_status d8_accumulate_weighted(d8_ctx* ctx, const uint8_t* dir, int64_t H, int
 /* Adjoint of d8_accumulate_weighted: for a loss L with dL/dA = dA,
  * dw(q) = dL/dw(q) = dA(q) + dw(down-slope neighbour of q), i.e. the sum of
  * dA over q's flow path (the transpose of Eq. 1).  Per-tile path sums, a
- * pointer-jumping solve over the tile exits, then a finalising pass.
- * fp32 in and out, compensated accumulation.  Errors as d8_accumulate. */
+ * pointer-jumping solve over the tile exits, then a finalising pass; the
+ * tiles are 32 x 32 whatever d8_set_tile says (their shared-memory need per
+ * cell makes larger tiles slower).  fp32 in and out, compensated
+ * accumulation.  Errors as d8_accumulate. */
 d8_status d8_accumulate_backward(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
                                  const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream);
 

@@ -505,7 +505,10 @@ d8_status d8_accumulate_backward(d8_ctx* c, const uint8_t* dir, int64_t H, int64
                                  const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream) {
   if (!c || bad_grid(dir, H, W, lddir) || bad_grid(dA, H, W, lddA) || bad_grid(dw, H, W, lddw)) return D8_ERR_ARG;
   cudaSetDevice(c->device);
-  const int T = c->T > 64 ? 64 : c->T;  // the path-doubling tile pass holds two buffers per cell
+  // The adjoint's tile passes double-buffer their pointer-jumping arrays (about
+  // 25 bytes of shared memory per cell), so they use 32 x 32 tiles whatever the
+  // context's tile side: larger tiles would leave too few tiles per SM.
+  const int T = 32;
   DemDesc d = make_desc(H, W, T);
   d.dir = const_cast<uint8_t*>(dir);
   d.lddir = lddir;

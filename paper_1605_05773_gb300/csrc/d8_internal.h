@@ -108,8 +108,8 @@ int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels);
 cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch);
 
 // unit-count tile passes (d8_unit.cu)
-cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, cudaStream_t s);
-cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, cudaStream_t s);
+cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s);
+cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s);
 
 // shared-memory bytes of the per-tile kernels (0 = configuration unsupported)
 size_t up_smem_bytes(int T, int mode);

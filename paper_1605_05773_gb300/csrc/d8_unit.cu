@@ -29,6 +29,8 @@
 //    only walks the paths down-slope of the perimeter cells that receive
 //    inflow from other tiles, adding that inflow along them, instead of
 //    re-running the whole tile.
+#include <type_traits>
+
 #include "d8_device.cuh"
 
 namespace d8 {
@@ -63,6 +65,10 @@ __device__ __forceinline__ int toff_tab(int k) {
 // bits and an index of 14, so there bits 15..18 hold the code instead and the
 // next cell is computed from it.
 constexpr uint32_t W_IN = 1u << 25, W_EXIT = 1u << 26, W_LEFT1 = 1u << 28;
+// Weighted tiles keep no count in the word: bits 0..7 hold which neighbours
+// are in-tile inputs (bit k: the input lies in direction k) and bit 27 marks a
+// cell present in the tile.  A source has no input and nothing left.
+constexpr uint32_t W_PRES = 1u << 27, W_SRC_W = 0xF0000000u | W_PRES | 0xFFu;
 template <int T>
 struct WL {
   static constexpr bool IDX = T <= 64;
@@ -95,19 +101,20 @@ __device__ __forceinline__ uint32_t col_off_mask(int j, int tw) {
 }
 
 // Per-cell bookkeeping once its code is known: the cell's own word (count 1,
-// next field, class bits) and, when its target is inside the tile, one more
-// input for the target.  A code 0..7 whose target is outside the tile is an
+// or the present bit for weighted tiles; next field; class bits) and, when its
+// target is inside the tile, one more input for the target (and, weighted,
+// the direction it arrives from).  A code 0..7 whose target is outside the tile is an
 // exit when the target cell (gi, gj) + offset is on the grid, otherwise the
 // path ends there; that test runs only for those perimeter cells.
-template <int T>
+template <int T, bool WT>
 __device__ __forceinline__ void add_cell(uint32_t* word, int c, int code, uint32_t off_mask, int64_t gi, int64_t gj,
                                          const DemDesc& d, uint32_t* status) {
   using W = WL<T>;
-  uint32_t own = 1u;
+  uint32_t own = WT ? W_PRES : 1u;
   if (code < 8) {
     if (!((off_mask >> code) & 1u)) {
       const int t = c + toff_tab<T>(code);
-      atomicAdd(&word[t], W_LEFT1);
+      atomicAdd(&word[t], W_LEFT1 | (WT ? 1u << opposite(code) : 0u));
       own |= W_IN | ((uint32_t)(W::IDX ? t : code) << W::CB);
     } else {
       const int64_t ti = gi + code_di(code), tj = gj + code_dj(code);
@@ -124,31 +131,36 @@ __device__ __forceinline__ void add_cell(uint32_t* word, int c, int code, uint32
   atomicAdd(&word[c], own);
 }
 
-template <int T>
+template <int T, bool WT>
 struct UpLayout {
   static constexpr size_t TT = (size_t)T * T;
   static constexpr size_t off_word = 0;
   static constexpr size_t off_seg = TT * 4;
   static constexpr size_t off_ring = off_seg + TT * 2;  // NWU rings of RING entries
   static constexpr size_t off_misc = off_ring + (size_t)NWU * RING * 2;
-  static constexpr size_t bytes = off_misc + 64;
+  static constexpr size_t off_val = off_misc + 64;  // weighted: float-float value per cell
+  static constexpr size_t bytes = off_val + (WT ? TT * sizeof(ff) : 0);
 };
 
-template <int T>
+// finalising pass: F is the inflow routed through each cell (uint32 counts;
+// double for weighted areas)
+template <int T, bool WT>
 struct FinLayout {
+  using F = typename std::conditional<WT, double, uint32_t>::type;
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t off_f = 0;                     // uint32 F per cell
-  static constexpr size_t off_code = TT * 4;             // uint8 code per cell
+  static constexpr size_t off_f = 0;                     // F per cell
+  static constexpr size_t off_code = TT * sizeof(F);     // uint8 code per cell
   static constexpr size_t off_rcell = off_code + TT;     // uint16 per perimeter slot
-  static constexpr size_t off_rin = off_rcell + (size_t)4 * T * 2;  // uint32 per slot
-  static constexpr size_t off_misc = off_rin + (size_t)4 * T * 4;
+  static constexpr size_t off_rin = (off_rcell + (size_t)4 * T * 2 + 15) / 16 * 16;  // F per slot
+  static constexpr size_t off_misc = off_rin + (size_t)4 * T * sizeof(F);
   static constexpr size_t bytes = off_misc + 64;
 };
 
 // Codes of tile g from a given direction field into word[], four consecutive
-// cells per thread per step (one 32-bit load when the layout allows).
-template <int T>
-__device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const TileGeo& g, uint32_t* word,
+// cells per thread per step (one 32-bit load when the layout allows); for a
+// weighted tile also the weights into val[].
+template <int T, bool WT>
+__device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const TileGeo& g, uint32_t* word, ff* val,
                                                     uint32_t* status) {
   constexpr int NQ = T * T / 4 / NTU;  // four-cell groups per thread
   const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
@@ -180,7 +192,13 @@ __device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const Tile
     for (int k = 0; k < 4; k++) {
       if (j + k >= g.tw) break;
       const int code = (four >> (8 * k)) & 0xFF;
-      add_cell<T>(word, c + k, code, rm | col_off_mask(j + k, g.tw), g.i0 + i, g.j0 + j + k, d, status);
+      add_cell<T, WT>(word, c + k, code, rm | col_off_mask(j + k, g.tw), g.i0 + i, g.j0 + j + k, d, status);
+    }
+    if (WT) {  // each cell's own weight starts its value
+      const float* wr = d.w + (g.i0 + i) * d.ldw + (g.j0 + j);
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (j + k < g.tw) val[c + k] = ff{__ldg(wr + k), 0.0f};
     }
   }
 }
@@ -207,16 +225,45 @@ __device__ __forceinline__ void store_counts(const DemDesc& d, const TileGeo& g,
   }
 }
 
+// Weighted: A[tile] = the in-tile areas held in val[], rounded to fp32.
 template <int T>
-__global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
-  using L = UpLayout<T>;
+__device__ __forceinline__ void store_areas(const DemDesc& d, const TileGeo& g, const ff* val) {
+  for (int q = threadIdx.x; q < T * T / 4; q += NTU) {
+    const int c = q * 4, i = c / T, j = c - i * T;
+    if (i >= g.th) continue;
+    float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
+    float o[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) o[k] = __fadd_rn(val[c + k].hi, val[c + k].lo);
+    if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+      *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (j + k < g.tw) dst[k] = o[k];
+    }
+  }
+}
+
+// Weighted value of a cell whose inputs have all arrived: its weight plus its
+// inputs' values, pulled in N..NW order with compensated adds (deterministic).
+template <int T>
+__device__ __forceinline__ ff pull_value(const ff* val, int c, uint32_t w) {
+  ff v = val[c];
+  for (uint32_t m = w & 0xFFu; m; m &= m - 1) v = ff_add(v, val[c + toff_tab<T>(__ffs(m) - 1)]);
+  return v;
+}
+
+template <int T, bool WT>
+__global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p) {
+  using L = UpLayout<T, WT>;
   using W = WL<T>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint32_t* word = reinterpret_cast<uint32_t*>(sm + L::off_word);
   uint16_t* seg = reinterpret_cast<uint16_t*>(sm + L::off_seg);
   uint16_t* ring = reinterpret_cast<uint16_t*>(sm + L::off_ring) + (threadIdx.x >> 5) * RING;
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
-  uint32_t* pval = static_cast<uint32_t*>(p.pval);
+  ff* val = reinterpret_cast<ff*>(sm + L::off_val);  // weighted only
   constexpr int TT = T * T;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -229,7 +276,7 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
     for (int c = threadIdx.x; c < TT / 4; c += NTU) w4[c] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) misc[0] = 0;
     __syncthreads();
-    tile_codes_from_dir<T>(d, g, word, p.status);  // Algorithm 1
+    tile_codes_from_dir<T, WT>(d, g, word, val, p.status);  // Algorithm 1
     __syncthreads();
     // Algorithm 2.  Every lane walks down-slope from a source while it is the
     // last input to arrive at the next cell; a lane whose walk stopped takes
@@ -238,15 +285,19 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
     // row at a time with a ballot.  A source is a cell with count 1 and no
     // input left (an absent cell of a ragged tile has count 0); the word of a
     // cell whose last input has arrived holds count >= 2, so a scan running
-    // behind the walks never takes it for one.
+    // behind the walks never takes it for one.  Weighted tiles carry values
+    // instead of counts: a finished cell stores its value before the atomic
+    // that publishes its arrival (block fence between), and the last arriver
+    // pulls its inputs' values after it (fence again).
     int done = 0;
     {
       int r = 0, head = 0, tail = 0, cur = -1, h = 0;
       uint32_t acc = 0, wv = 0;
+      ff v{0.0f, 0.0f};
       for (;;) {
         while (tail - head < 32 && r < TT / NTU) {  // at most RING - 1 pending
           const int c = threadIdx.x + r * NTU;
-          const bool src = (word[c] & W::SRC_MASK) == 1u;
+          const bool src = WT ? (word[c] & W_SRC_W) == W_PRES : (word[c] & W::SRC_MASK) == 1u;
           const unsigned m = __ballot_sync(FULL, src);
           if (src) ring[(tail + __popc(m & lt)) & (RING - 1)] = (uint16_t)c;
           tail += __popc(m);
@@ -261,6 +312,7 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
             h = cur;
             wv = word[cur];
             acc = 1;  // a source
+            if (WT) v = val[cur];  // its weight
             done++;
           }
           head = min(head + __popc(need), tail);
@@ -268,12 +320,21 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
           break;
         }
         if (cur >= 0) {
+          if (WT) {
+            val[cur] = v;
+            __threadfence_block();
+          }
           if (wv & W_IN) {
             const int s = W::next(wv, cur);
-            const uint32_t old = atomicAdd(&word[s], acc - W_LEFT1);
+            const uint32_t old = atomicAdd(&word[s], WT ? 0u - W_LEFT1 : acc - W_LEFT1);
             if (W::last(old)) {  // last input to arrive: continue there
               seg[s] = (uint16_t)h;
-              acc += W::cnt(old);
+              if (WT) {
+                __threadfence_block();
+                v = pull_value<T>(val, s, old);
+              } else {
+                acc += W::cnt(old);
+              }
               wv = old;
               cur = s;
               done++;
@@ -293,19 +354,26 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
     __syncthreads();
     const bool cyc = misc[0] != g.th * g.tw;
     if (threadIdx.x == 0 && cyc) set_status(p.status, D8_ERR_CYCLE);
-    // in-tile counts (inflow from other tiles = 0) go to A now; the finalising
-    // pass adds the inflow only where some reaches
-    store_counts<T>(d, g, word);
+    // in-tile counts / areas (inflow from other tiles = 0) go to A now; the
+    // finalising pass adds the inflow only where some reaches
+    if (WT)
+      store_areas<T>(d, g, val);
+    else
+      store_counts<T>(d, g, word);
     // perimeter summary: the exit of each perimeter cell's in-tile path, by a
     // chase over segment records (resolved records are written back)
     for (int s = threadIdx.x; s < 4 * T; s += NTU) {
       int i, j;
       uint16_t pe = PEX_TERM;
       uint32_t pv = 0;
+      ff pvw{0.0f, 0.0f};
       if (slot_cell(s, g.th, g.tw, T, i, j)) {
         const int c = i * T + j;
         const uint32_t w = word[c];
-        pv = W::cnt(w);
+        if (WT)
+          pvw = val[c];
+        else
+          pv = W::cnt(w);
         if (w & W_EXIT) {
           pe = (uint16_t)(PEX_EXIT | W::code(w));
         } else if ((w & W_IN) && !cyc) {
@@ -328,7 +396,10 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
         }
       }
       p.pex[t * (4 * T) + s] = pe;
-      pval[t * (4 * T) + s] = pv;
+      if (WT)
+        static_cast<ff*>(p.pval)[t * (4 * T) + s] = pvw;
+      else
+        static_cast<uint32_t*>(p.pval)[t * (4 * T) + s] = pv;
     }
   }
 }
@@ -345,21 +416,29 @@ __global__ void __launch_bounds__(NTU, 8) k_up_unit(DemTable dt, Pipe p) {
 // receiver (about a sixth of a 64 x 64 tile on fractal terrain) are touched.
 // The work is the summed length of the receivers' in-tile paths (at most
 // 4T * T^2 for adversarial fields, about the sub-forest size on terrain).
-template <int T>
-__global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
-  using L = FinLayout<T>;
+// Weighted: the same with double inflow sums (the combine's float-float exit
+// values enter exactly), and A = fp32(A + F) where F is nonzero.
+__device__ __forceinline__ uint32_t fin_in(uint32_t x) { return x; }
+__device__ __forceinline__ double fin_in(ff x) { return (double)x.hi + (double)x.lo; }
+
+template <int T, bool WT>
+__global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe p) {
+  using L = FinLayout<T, WT>;
+  using FV = typename L::F;
+  using XV = typename std::conditional<WT, ff, uint32_t>::type;
   extern __shared__ __align__(16) unsigned char sm[];
-  uint32_t* F = reinterpret_cast<uint32_t*>(sm + L::off_f);
+  FV* F = reinterpret_cast<FV*>(sm + L::off_f);
   uint8_t* code = sm + L::off_code;
   uint16_t* rcell = reinterpret_cast<uint16_t*>(sm + L::off_rcell);
-  uint32_t* rin = reinterpret_cast<uint32_t*>(sm + L::off_rin);
+  FV* rin = reinterpret_cast<FV*>(sm + L::off_rin);
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
-  const uint32_t* xval = static_cast<const uint32_t*>(p.S);
+  const XV* xval = static_cast<const XV*>(p.S);
   constexpr int TT = T * T;
 
   // F[] starts at zero; every tile leaves it at zero again (the output pass
   // clears the words the walks touched)
-  for (int c = threadIdx.x; c < TT / 4; c += NTF) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
+  for (int c = threadIdx.x; c < (int)(TT * sizeof(FV) / 16); c += NTF)
+    reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) misc[0] = 0;
 
   TileQueue tq(p.queue + 1, p.ntiles);
@@ -388,7 +467,8 @@ __global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
     for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
-      uint32_t in = 0;
+      FV in = 0;
+      bool any = false;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         const int li = i + code_di(k), lj = j + code_dj(k);
@@ -396,9 +476,10 @@ __global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
         const int64_t gi = g.i0 + li, gj = g.j0 + lj;
         if (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) continue;
         if (d.dir[gi * d.lddir + gj] != opposite(k)) continue;
-        in += xval[global_slot(d, gi, gj, T)];
+        in += fin_in(xval[global_slot(d, gi, gj, T)]);
+        any = true;
       }
-      if (in) {
+      if (any) {
         const int r = atomicAdd(&misc[0], 1);
         rcell[r] = (uint16_t)(i * T + j);
         rin[r] = in;
@@ -410,7 +491,7 @@ __global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
     // T^2 cells; the bound only matters for a field with a cycle, which the
     // first pass reports)
     for (int r = threadIdx.x; r < nrec; r += NTF) {
-      const uint32_t in = rin[r];
+      const FV in = rin[r];
       int c = rcell[r], i = c / T, j = c & (T - 1);
       atomicAdd(&F[c], in);
       for (int step = 0; step < TT; step++) {
@@ -426,25 +507,52 @@ __global__ void __launch_bounds__(NTF) k_fin_unit(DemTable dt, Pipe p) {
     __syncthreads();
     if (threadIdx.x == 0) misc[0] = 0;
     // A += F where F is nonzero; touched words go back to zero
-    for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-      const uint4 f = reinterpret_cast<const uint4*>(F)[q];
-      if (!(f.x | f.y | f.z | f.w)) continue;
-      reinterpret_cast<uint4*>(F)[q] = make_uint4(0, 0, 0, 0);
-      const int c = q * 4, i = c / T, j = c - i * T;
-      if (i >= g.th) continue;
-      uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
-      if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-        uint4 a = *reinterpret_cast<uint4*>(dst);
-        a.x += f.x;
-        a.y += f.y;
-        a.z += f.z;
-        a.w += f.w;
-        *reinterpret_cast<uint4*>(dst) = a;
-      } else {
-        const uint32_t fv[4] = {f.x, f.y, f.z, f.w};
+    if (!WT) {
+      uint32_t* F32 = reinterpret_cast<uint32_t*>(F);
+      for (int q = threadIdx.x; q < TT / 4; q += NTF) {
+        const uint4 f = reinterpret_cast<const uint4*>(F32)[q];
+        if (!(f.x | f.y | f.z | f.w)) continue;
+        reinterpret_cast<uint4*>(F32)[q] = make_uint4(0, 0, 0, 0);
+        const int c = q * 4, i = c / T, j = c - i * T;
+        if (i >= g.th) continue;
+        uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
+        if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+          uint4 a = *reinterpret_cast<uint4*>(dst);
+          a.x += f.x;
+          a.y += f.y;
+          a.z += f.z;
+          a.w += f.w;
+          *reinterpret_cast<uint4*>(dst) = a;
+        } else {
+          const uint32_t fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-          if (j + k < g.tw && fv[k]) dst[k] += fv[k];
+          for (int k = 0; k < 4; k++)
+            if (j + k < g.tw && fv[k]) dst[k] += fv[k];
+        }
+      }
+    } else {
+      double2* F2 = reinterpret_cast<double2*>(F);
+      for (int q = threadIdx.x; q < TT / 4; q += NTF) {
+        const double2 fa = F2[2 * q], fb = F2[2 * q + 1];
+        const double f[4] = {fa.x, fa.y, fb.x, fb.y};
+        if (f[0] == 0.0 && f[1] == 0.0 && f[2] == 0.0 && f[3] == 0.0) continue;
+        F2[2 * q] = make_double2(0.0, 0.0);
+        F2[2 * q + 1] = make_double2(0.0, 0.0);
+        const int c = q * 4, i = c / T, j = c - i * T;
+        if (i >= g.th) continue;
+        float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
+        if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+          float4 a = *reinterpret_cast<float4*>(dst);
+          float* av = reinterpret_cast<float*>(&a);
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (f[k] != 0.0) av[k] = __double2float_rn((double)av[k] + f[k]);
+          *reinterpret_cast<float4*>(dst) = a;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if (j + k < g.tw && f[k] != 0.0) dst[k] = __double2float_rn((double)dst[k] + f[k]);
+        }
       }
     }
   }
@@ -464,40 +572,46 @@ static unsigned persistent_grid_u(K kernel, int threads, size_t smem, int64_t nt
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-template <int T>
+template <int T, bool WT>
 static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
-  const size_t bytes = UpLayout<T>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_up_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const size_t bytes = UpLayout<T, WT>::bytes;
+  auto k = k_up_unit<T, WT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_up_unit<T><<<persistent_grid_u(k_up_unit<T>, NTU, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
+  k<<<persistent_grid_u(k, NTU, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
-template <int T>
+template <int T, bool WT>
 static cudaError_t launch_down_unit_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
-  const size_t bytes = FinLayout<T>::bytes;
-  cudaError_t e = cudaFuncSetAttribute(k_fin_unit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const size_t bytes = FinLayout<T, WT>::bytes;
+  auto k = k_fin_unit<T, WT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_fin_unit<T><<<persistent_grid_u(k_fin_unit<T>, NTF, bytes, p.ntiles), NTF, bytes, s>>>(dt, p);
+  k<<<persistent_grid_u(k, NTF, bytes, p.ntiles), NTF, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
 }  // namespace unit
 
-cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, cudaStream_t s) {
+cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s) {
   switch (p.T) {
-    case 32: return unit::launch_up_unit_t<32>(dt, p, s);
-    case 64: return unit::launch_up_unit_t<64>(dt, p, s);
-    case 128: return unit::launch_up_unit_t<128>(dt, p, s);
+    case 32: return weighted ? unit::launch_up_unit_t<32, true>(dt, p, s) : unit::launch_up_unit_t<32, false>(dt, p, s);
+    case 64: return weighted ? unit::launch_up_unit_t<64, true>(dt, p, s) : unit::launch_up_unit_t<64, false>(dt, p, s);
+    case 128:
+      return weighted ? unit::launch_up_unit_t<128, true>(dt, p, s) : unit::launch_up_unit_t<128, false>(dt, p, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, cudaStream_t s) {
+cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s) {
   switch (p.T) {
-    case 32: return unit::launch_down_unit_t<32>(dt, p, s);
-    case 64: return unit::launch_down_unit_t<64>(dt, p, s);
-    case 128: return unit::launch_down_unit_t<128>(dt, p, s);
+    case 32:
+      return weighted ? unit::launch_down_unit_t<32, true>(dt, p, s) : unit::launch_down_unit_t<32, false>(dt, p, s);
+    case 64:
+      return weighted ? unit::launch_down_unit_t<64, true>(dt, p, s) : unit::launch_down_unit_t<64, false>(dt, p, s);
+    case 128:
+      return weighted ? unit::launch_down_unit_t<128, true>(dt, p, s) : unit::launch_down_unit_t<128, false>(dt, p, s);
   }
   return cudaErrorInvalidValue;
 }
