@@ -143,10 +143,10 @@ struct UpLayout {
 };
 
 // finalising pass: F is the inflow routed through each cell (uint32 counts;
-// double for weighted areas)
+// float-float {hi, lo} for weighted areas)
 template <int T, bool WT>
 struct FinLayout {
-  using F = typename std::conditional<WT, double, uint32_t>::type;
+  using F = typename std::conditional<WT, float2, uint32_t>::type;
   static constexpr size_t TT = (size_t)T * T;
   static constexpr size_t off_f = 0;                     // F per cell
   static constexpr size_t off_code = TT * sizeof(F);     // uint8 code per cell
@@ -416,10 +416,22 @@ __global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p
 // receiver (about a sixth of a 64 x 64 tile on fractal terrain) are touched.
 // The work is the summed length of the receivers' in-tile paths (at most
 // 4T * T^2 for adversarial fields, about the sub-forest size on terrain).
-// Weighted: the same with double inflow sums (the combine's float-float exit
-// values enter exactly), and A = fp32(A + F) where F is nonzero.
+// Weighted: the same with float-float inflow sums, and A = fp32(A + F) where F
+// is nonzero.  Shared atomics exist natively for fp32 but not for 64-bit
+// values, so F is kept as {hi, lo}: the atomic add of the inflow's high part
+// returns the old value, from which the add's exact rounding error follows
+// (TwoSum), and that error goes with the inflow's low part into lo by a
+// second fp32 atomic.  Only the rounding of lo's own sums is lost.
 __device__ __forceinline__ uint32_t fin_in(uint32_t x) { return x; }
 __device__ __forceinline__ double fin_in(ff x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ void fin_add(uint32_t* F, int c, uint32_t x) { atomicAdd(&F[c], x); }
+__device__ __forceinline__ void fin_add(float2* F, int c, float2 x) {
+  const float old = atomicAdd(&F[c].x, x.x);
+  const float s = __fadd_rn(old, x.x);
+  const float bv = __fsub_rn(s, old);
+  const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bv)), __fsub_rn(x.x, bv));
+  atomicAdd(&F[c].y, __fadd_rn(err, x.y));
+}
 
 template <int T, bool WT>
 __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe p) {
@@ -467,7 +479,7 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
     for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
-      FV in = 0;
+      typename std::conditional<WT, double, uint32_t>::type in = 0;
       bool any = false;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
@@ -482,7 +494,12 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
       if (any) {
         const int r = atomicAdd(&misc[0], 1);
         rcell[r] = (uint16_t)(i * T + j);
-        rin[r] = in;
+        if constexpr (WT) {
+          const float hi = __double2float_rn((double)in);
+          rin[r] = FV{hi, __double2float_rn((double)in - (double)hi)};
+        } else {
+          rin[r] = in;
+        }
       }
     }
     __syncthreads();
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
     for (int r = threadIdx.x; r < nrec; r += NTF) {
       const FV in = rin[r];
       int c = rcell[r], i = c / T, j = c & (T - 1);
-      atomicAdd(&F[c], in);
+      fin_add(F, c, in);
       for (int step = 0; step < TT; step++) {
         const int k = code[c];
         if (k >= 8) break;
@@ -501,7 +518,7 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
         j += code_dj(k);
         if ((unsigned)i >= (unsigned)g.th || (unsigned)j >= (unsigned)g.tw) break;
         c = i * T + j;
-        atomicAdd(&F[c], in);
+        fin_add(F, c, in);
       }
     }
     __syncthreads();
@@ -531,13 +548,16 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
         }
       }
     } else {
-      double2* F2 = reinterpret_cast<double2*>(F);
+      float4* F4 = reinterpret_cast<float4*>(F);
       for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-        const double2 fa = F2[2 * q], fb = F2[2 * q + 1];
-        const double f[4] = {fa.x, fa.y, fb.x, fb.y};
-        if (f[0] == 0.0 && f[1] == 0.0 && f[2] == 0.0 && f[3] == 0.0) continue;
-        F2[2 * q] = make_double2(0.0, 0.0);
-        F2[2 * q + 1] = make_double2(0.0, 0.0);
+        const float4 fa = F4[2 * q], fb = F4[2 * q + 1];  // {hi, lo} of four cells
+        const double f[4] = {(double)fa.x + (double)fa.y, (double)fa.z + (double)fa.w, (double)fb.x + (double)fb.y,
+                             (double)fb.z + (double)fb.w};
+        if (fa.x == 0.f && fa.y == 0.f && fa.z == 0.f && fa.w == 0.f && fb.x == 0.f && fb.y == 0.f && fb.z == 0.f &&
+            fb.w == 0.f)
+          continue;  // (raw parts: a {hi, lo} that cancels must still be cleared)
+        F4[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        F4[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         const int c = q * 4, i = c / T, j = c - i * T;
         if (i >= g.th) continue;
         float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
