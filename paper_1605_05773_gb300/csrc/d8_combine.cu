@@ -37,11 +37,10 @@ constexpr uint16_t N_NONE = 0xFFFDu;  // not an exit slot
 template <int S, int G, class V>
 struct GroupLayout {
   static constexpr int NS = G * G * 4 * S;  // child slots of a group
-  static constexpr size_t off_spx = 0;                      // u16 child exit codes
-  static constexpr size_t off_par = off_spx + (size_t)NS * 2;  // u16 parent node
-  static constexpr size_t off_val = (off_par + (size_t)NS * 2 + 15) / 16 * 16;  // value
-  static constexpr size_t off_deg = off_val + (size_t)NS * sizeof(V);  // u32 unfinished children
-  static constexpr size_t off_src = off_deg + (size_t)NS * 4;  // u16 source lists
+  static constexpr size_t off_spx = 0;                                       // u16 child exit codes
+  static constexpr size_t off_val = ((size_t)NS * 2 + 15) / 16 * 16;         // value
+  static constexpr size_t off_pd = off_val + (size_t)NS * sizeof(V);         // u32 parent << 16 | children left
+  static constexpr size_t off_src = off_pd + (size_t)NS * 4;                 // u16 source lists
   static constexpr size_t off_misc = off_src + (size_t)NS * 2;
   static constexpr size_t bytes = off_misc + 64;
 };
@@ -70,9 +69,15 @@ __device__ __forceinline__ UnitGeo unit_geo(const DemDesc& d, int64_t uy, int64_
 // Load the children of group (gy, gx) and compute every child exit's parent
 // inside the group and the children count of every node.
 // Returns the number of child exits this thread loaded.
+// pd[n]: node n's parent (bits 16..31, or N_ROOT / N_OUT / N_NONE) and its
+// number of unfinished children (bits 0..15; a group has fewer than 2^16
+// nodes), one 32-bit word so that both live in native 32-bit atomics.
+__device__ __forceinline__ uint32_t pd_par(uint32_t w) { return w >> 16; }
+__device__ __forceinline__ uint32_t pd_deg(uint32_t w) { return w & 0xFFFFu; }
+
 template <int S, int G, class V, class CV>
 __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint16_t* cpex, const CV* cpval,
-                          uint16_t* spx, uint16_t* par, V* val, uint32_t* deg) {
+                          uint16_t* spx, V* val, uint32_t* pd) {
   constexpr int NS = G * G * 4 * S;
   int exits = 0;
   for (int n = threadIdx.x; n < NS; n += NTG) {
@@ -90,7 +95,7 @@ __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint1
     }
     spx[n] = pe;
     val[n] = v;
-    deg[n] = 0;
+    pd[n] = 0;
   }
   __syncthreads();
   for (int n = threadIdx.x; n < NS; n += NTG) {
@@ -117,12 +122,12 @@ __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint1
           pr = N_ROOT;
         else
           pr = (uint16_t)(lt2 * (4 * S) + pe2);
-        if (pr < N_NONE) atomicAdd(&deg[pr], 1u);
+        if (pr < N_NONE) atomicAdd(&pd[pr], 1u);
       } else {
         pr = N_OUT;
       }
     }
-    par[n] = pr;
+    if (pr != 0) atomicAdd(&pd[n], (uint32_t)pr << 16);
   }
   __syncthreads();
   return exits;
@@ -134,7 +139,7 @@ __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint1
 // the last child continues at the parent (after a fence, so it sees every
 // child's addition).  Returns the number of nodes this thread finished.
 template <int S, int G, class V>
-__device__ int group_walk(uint16_t* spx, const uint16_t* par, V* val, uint32_t* deg, uint16_t* srcl) {
+__device__ int group_walk(uint16_t* spx, V* val, uint32_t* pd, uint16_t* srcl) {
   constexpr int NS = G * G * 4 * S;
   constexpr int NW = NTG / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -142,7 +147,7 @@ __device__ int group_walk(uint16_t* spx, const uint16_t* par, V* val, uint32_t* 
   int n = 0;
   for (int r = 0; r < NS / NTG; r++) {
     const int c = threadIdx.x + r * NTG;
-    const bool s = (spx[c] & PEX_EXIT) && deg[c] == 0u;
+    const bool s = (spx[c] & PEX_EXIT) && pd_deg(pd[c]) == 0u;
     const unsigned m = __ballot_sync(FULL, s);
     if (s) my[n + __popc(m & ((1u << lane) - 1u))] = (uint16_t)c;
     n += __popc(m);
@@ -165,15 +170,15 @@ __device__ int group_walk(uint16_t* spx, const uint16_t* par, V* val, uint32_t* 
       break;
     }
     if (cur >= 0) {
-      const uint16_t p = par[cur];
+      const uint32_t p = pd_par(pd[cur]);
       if (p >= N_NONE) {
         cur = -1;
         continue;
       }
       atomicAdd(&val[p], v);
       __threadfence_block();
-      const uint32_t old = atomicSub(&deg[p], 1u);
-      if (old == 1u) {
+      const uint32_t old = atomicSub(&pd[p], 1u);
+      if (pd_deg(old) == 1u) {
         __threadfence_block();
         cur = p;
         v = *(volatile V*)&val[p];
@@ -193,9 +198,8 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
   using L = GroupLayout<S, G, V>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint16_t* spx = reinterpret_cast<uint16_t*>(sm + L::off_spx);
-  uint16_t* par = reinterpret_cast<uint16_t*>(sm + L::off_par);
   V* val = reinterpret_cast<V*>(sm + L::off_val);
-  uint32_t* deg = reinterpret_cast<uint32_t*>(sm + L::off_deg);
+  uint32_t* pd = reinterpret_cast<uint32_t*>(sm + L::off_pd);
   uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
   constexpr int NS = L::NS;
@@ -211,8 +215,8 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
       misc[0] = 0;
       misc[1] = 0;
     }
-    const int exits = group_load<S, G, V, CV>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
-    const int done = group_walk<S, G, V>(spx, par, val, deg, srcl);
+    const int exits = group_load<S, G, V, CV>(cd, gy, gx, cpex, cpval, spx, val, pd);
+    const int done = group_walk<S, G, V>(spx, val, pd, srcl);
     atomicAdd(&misc[0], done);
     atomicAdd(&misc[1], exits);
     __syncthreads();
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
         const uint16_t pe = spx[n0];
         int x = -1;
         if (pe & PEX_EXIT) {
-          if (par[n0] == N_OUT) {
+          if (pd_par(pd[n0]) == N_OUT) {
             gpe = (uint16_t)(PEX_EXIT | (pe & 7));
             gv = val[n0];
           } else {
@@ -242,8 +246,8 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
           x = lt * (4 * S) + pe;
         }
         if (x >= 0) {
-          for (int it = 0; it < NS && par[x] < N_NONE; it++) x = par[x];
-          if (par[x] == N_OUT) {
+          for (int it = 0; it < NS && pd_par(pd[x]) < N_NONE; it++) x = (int)pd_par(pd[x]);
+          if (pd_par(pd[x]) == N_OUT) {
             const int xlt = x / (4 * S), xs = x - xlt * (4 * S);
             const UnitGeo xu = unit_geo(cd, gy * G + xlt / G, gx * G + xlt % G, S);
             int xi, xj;
@@ -265,9 +269,8 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
   using L = GroupLayout<S, G, V>;
   extern __shared__ __align__(16) unsigned char sm[];
   uint16_t* spx = reinterpret_cast<uint16_t*>(sm + L::off_spx);
-  uint16_t* par = reinterpret_cast<uint16_t*>(sm + L::off_par);
   V* val = reinterpret_cast<V*>(sm + L::off_val);
-  uint32_t* deg = reinterpret_cast<uint32_t*>(sm + L::off_deg);
+  uint32_t* pd = reinterpret_cast<uint32_t*>(sm + L::off_pd);
   uint16_t* srcl = reinterpret_cast<uint16_t*>(sm + L::off_src);
   constexpr int NS = L::NS;
   constexpr int GS = G * S;
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
     const DemDesc cd = dem_by_index(cdt, dem);
     const int64_t lg = gu - gd.tile_base;
     const int64_t gy = lg / gd.ntx, gx = lg % gd.ntx;
-    group_load<S, G, V, CV>(cd, gy, gx, cpex, cpval, spx, par, val, deg);
+    group_load<S, G, V, CV>(cd, gy, gx, cpex, cpval, spx, val, pd);
     // inflow across the group border: each border cell r receives the final
     // areas of the outside cells draining into it; the inflow then follows
     // r's path inside its child unit to that child's exit
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
         atomicAdd(&val[lt * (4 * S) + pe], in);
     }
     __syncthreads();
-    group_walk<S, G, V>(spx, par, val, deg, srcl);
+    group_walk<S, G, V>(spx, val, pd, srcl);
     __syncthreads();
     for (int n = threadIdx.x; n < NS; n += NTG) {
       if (!(spx[n] & PEX_EXIT)) continue;
@@ -355,10 +358,21 @@ __global__ void k_top_init(DemTable dt, const uint16_t* pex, const CV* pval, V* 
 
 __global__ void k_top_sources(const uint16_t* pex, const uint32_t* deg, uint32_t* list, uint32_t* counters,
                               int64_t nslots) {
+  // one atomic per warp on each counter (they are shared by the whole grid)
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
-    if ((pex[g] & PEX_EXIT) && deg[g] == 0u) list[atomicAdd(&counters[0], 1u)] = (uint32_t)g;
-    if (pex[g] & PEX_EXIT) atomicAdd(&counters[1], 1u);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < nslots; b += stride) {
+    const int64_t g = b + lane;
+    const bool ex = g < nslots && (pex[g] & PEX_EXIT);
+    const bool src = ex && deg[g] == 0u;
+    const unsigned ms = __ballot_sync(0xFFFFFFFFu, src), me = __ballot_sync(0xFFFFFFFFu, ex);
+    uint32_t base = 0;
+    if (lane == 0) {
+      if (ms) base = atomicAdd(&counters[0], (uint32_t)__popc(ms));
+      if (me) atomicAdd(&counters[1], (uint32_t)__popc(me));
+    }
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (src) list[base + __popc(ms & ((1u << lane) - 1u))] = (uint32_t)g;
   }
 }
 
