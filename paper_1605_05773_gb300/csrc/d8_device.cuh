@@ -61,28 +61,6 @@ struct VOps<uint32_t> {
   static __device__ __forceinline__ bool nonzero(uint32_t v) { return v != 0u; }
 };
 
-template <>
-struct VOps<ff> {
-  static __device__ __forceinline__ ff zero() { return ff{0.0f, 0.0f}; }
-  static __device__ __forceinline__ ff add(ff a, ff b) { return ff_add(a, b); }
-  // lock-free compensated add: CAS on the 64-bit (hi, lo) pair
-  static __device__ __forceinline__ void atomic_add(ff* p, ff v) {
-    unsigned long long* q = reinterpret_cast<unsigned long long*>(p);
-    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(q);
-    for (;;) {
-      ff cur;
-      cur.hi = __uint_as_float((uint32_t)old);
-      cur.lo = __uint_as_float((uint32_t)(old >> 32));
-      const ff nv = ff_add(cur, v);
-      const unsigned long long nb =
-          (unsigned long long)__float_as_uint(nv.hi) | ((unsigned long long)__float_as_uint(nv.lo) << 32);
-      const unsigned long long prev = atomicCAS(q, old, nb);
-      if (prev == old) break;
-      old = prev;
-    }
-  }
-  static __device__ __forceinline__ bool nonzero(ff v) { return v.hi != 0.0f || v.lo != 0.0f; }
-};
 
 // DEM of a tile, by value so its fields can live in registers
 __device__ __forceinline__ DemDesc dem_of(const DemTable& t, int64_t tile) {
@@ -161,7 +139,6 @@ constexpr uint8_t CL_IN = 0x08;      // target inside the tile; bits 0..2 = code
 constexpr uint8_t CL_EXIT = 0x10;    // target in another tile; bits 0..2 = code
 constexpr uint8_t CL_TERM = 0x20;    // path ends here
 constexpr uint8_t CL_ABSENT = 0x40;  // outside a ragged tile
-constexpr uint16_t JP_TERM = 0xFFFFu;
 
 // Classify a code of cell (i, j) of a tile: in-tile target, exit, or end.
 __device__ __forceinline__ uint8_t classify(int code, int i, int j, const TileGeo& g, const DemDesc& d,

@@ -146,11 +146,11 @@ static cudaError_t launch_combine_fwd_t(const DemTable& dt, const Pipe& p, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine_fwd(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch) {
+cudaError_t launch_combine_flat(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch) {
   switch (p.T) {
-    case 32: return weighted ? launch_combine_fwd_t<32, ff>(dt, p, s, nlaunch) : launch_combine_fwd_t<32, uint32_t>(dt, p, s, nlaunch);
-    case 64: return weighted ? launch_combine_fwd_t<64, ff>(dt, p, s, nlaunch) : launch_combine_fwd_t<64, uint32_t>(dt, p, s, nlaunch);
-    case 128: return weighted ? launch_combine_fwd_t<128, ff>(dt, p, s, nlaunch) : launch_combine_fwd_t<128, uint32_t>(dt, p, s, nlaunch);
+    case 32: return launch_combine_fwd_t<32, uint32_t>(dt, p, s, nlaunch);
+    case 64: return launch_combine_fwd_t<64, uint32_t>(dt, p, s, nlaunch);
+    case 128: return launch_combine_fwd_t<128, uint32_t>(dt, p, s, nlaunch);
   }
   return cudaErrorInvalidValue;
 }

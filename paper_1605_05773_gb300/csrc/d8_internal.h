@@ -62,7 +62,8 @@ struct Pipe {
 cudaError_t launch_flowdir(const DemTable& dt, int64_t ntiles, int T, int rule, uint32_t* status, cudaStream_t s,
                            int* nlaunch);
 cudaError_t launch_up(const DemTable& dt, const Pipe& p, int mode, int rule, cudaStream_t s, int* nlaunch);
-cudaError_t launch_combine_fwd(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch);
+// flat pointer-jumping combine of unit counts (the allocation-free entry point)
+cudaError_t launch_combine_flat(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_down(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch);
 cudaError_t launch_bwd_up(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_combine_bwd(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);

@@ -139,7 +139,7 @@ extern "C" d8_status d8_flowdir_accumulate_noalloc(const float* z, int64_t H, in
   dt.ndem = 1;
   int n = 0;
   e = d8::launch_up(dt, p, d8::UP_UNIT_Z, (int)rule, s, &n);
-  if (e == cudaSuccess) e = d8::launch_combine_fwd(dt, p, false, s, &n);
+  if (e == cudaSuccess) e = d8::launch_combine_flat(dt, p, s, &n);
   if (e == cudaSuccess) e = d8::launch_down(dt, p, false, s, &n);
   return cuda_rc(e);
 }

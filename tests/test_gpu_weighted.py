@@ -20,7 +20,7 @@ def grad_error(g32, d_ref, c):
     return (np.abs(g32.astype(np.float64) - G64) / scale).max(), G64
 
 
-@pytest.mark.parametrize("T", [32, 64])
+@pytest.mark.parametrize("T", [32, 64, 128])
 @pytest.mark.parametrize("shape", [(1, 1), (3, 5), (97, 131), (300, 257), (520, 130)])
 def test_weighted_and_backward_small(d8, T, shape):
     d8.set_tile(T)
