@@ -142,19 +142,32 @@ struct UpLayout {
   static constexpr size_t bytes = off_val + (WT ? TT * sizeof(ff) : 0);
 };
 
-// finalising pass: F is the inflow routed through each cell (uint32 counts;
-// float-float {hi, lo} for weighted areas)
-template <int T, bool WT>
+// finalising pass, unit counts: F is the inflow routed through each cell
+template <int T>
 struct FinLayout {
-  using F = typename std::conditional<WT, float2, uint32_t>::type;
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t off_f = 0;                     // F per cell
-  static constexpr size_t off_code = TT * sizeof(F);     // uint8 code per cell
+  static constexpr size_t off_f = 0;                     // uint32 F per cell
+  static constexpr size_t off_code = TT * 4;             // uint8 code per cell
   static constexpr size_t off_rcell = off_code + TT;     // uint16 per perimeter slot
-  static constexpr size_t off_rin = (off_rcell + (size_t)4 * T * 2 + 15) / 16 * 16;  // F per slot
-  static constexpr size_t off_misc = off_rin + (size_t)4 * T * sizeof(F);
+  static constexpr size_t off_rin = off_rcell + (size_t)4 * T * 2;  // uint32 per slot
+  static constexpr size_t off_misc = off_rin + (size_t)4 * T * 4;
   static constexpr size_t bytes = off_misc + 64;
 };
+
+// finalising pass, weighted: float-float F per cell and a mark word per cell
+// (bits 0..7: which neighbours are inputs carrying inflow; 8..15: how many of
+// them are still to arrive; 16: the cell is a receiver)
+template <int T>
+struct FinWLayout {
+  static constexpr size_t TT = (size_t)T * T;
+  static constexpr size_t off_f = 0;                     // ff per cell
+  static constexpr size_t off_mk = TT * sizeof(ff);      // uint32 per cell
+  static constexpr size_t off_code = off_mk + TT * 4;    // uint8 code per cell
+  static constexpr size_t off_rcell = off_code + TT;     // uint16 per perimeter slot
+  static constexpr size_t off_misc = (off_rcell + (size_t)4 * T * 2 + 15) / 16 * 16;
+  static constexpr size_t bytes = off_misc + 64;
+};
+constexpr uint32_t MK_CNT1 = 1u << 8, MK_REC = 1u << 16;
 
 // Codes of tile g from a given direction field into word[], four consecutive
 // cells per thread per step (one 32-bit load when the layout allows); for a
@@ -416,41 +429,21 @@ __global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p
 // receiver (about a sixth of a 64 x 64 tile on fractal terrain) are touched.
 // The work is the summed length of the receivers' in-tile paths (at most
 // 4T * T^2 for adversarial fields, about the sub-forest size on terrain).
-// Weighted: the same with float-float inflow sums, and A = fp32(A + F) where F
-// is nonzero.  Shared atomics exist natively for fp32 but not for 64-bit
-// values, so F is kept as {hi, lo}: the atomic add of the inflow's high part
-// returns the old value, from which the add's exact rounding error follows
-// (TwoSum), and that error goes with the inflow's low part into lo by a
-// second fp32 atomic.  Only the rounding of lo's own sums is lost.
-__device__ __forceinline__ uint32_t fin_in(uint32_t x) { return x; }
-__device__ __forceinline__ double fin_in(ff x) { return (double)x.hi + (double)x.lo; }
-__device__ __forceinline__ void fin_add(uint32_t* F, int c, uint32_t x) { atomicAdd(&F[c], x); }
-__device__ __forceinline__ void fin_add(float2* F, int c, float2 x) {
-  const float old = atomicAdd(&F[c].x, x.x);
-  const float s = __fadd_rn(old, x.x);
-  const float bv = __fsub_rn(s, old);
-  const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bv)), __fsub_rn(x.x, bv));
-  atomicAdd(&F[c].y, __fadd_rn(err, x.y));
-}
-
-template <int T, bool WT>
-__global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe p) {
-  using L = FinLayout<T, WT>;
-  using FV = typename L::F;
-  using XV = typename std::conditional<WT, ff, uint32_t>::type;
+template <int T>
+__global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
+  using L = FinLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
-  FV* F = reinterpret_cast<FV*>(sm + L::off_f);
+  uint32_t* F = reinterpret_cast<uint32_t*>(sm + L::off_f);
   uint8_t* code = sm + L::off_code;
   uint16_t* rcell = reinterpret_cast<uint16_t*>(sm + L::off_rcell);
-  FV* rin = reinterpret_cast<FV*>(sm + L::off_rin);
+  uint32_t* rin = reinterpret_cast<uint32_t*>(sm + L::off_rin);
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
-  const XV* xval = static_cast<const XV*>(p.S);
+  const uint32_t* xval = static_cast<const uint32_t*>(p.S);
   constexpr int TT = T * T;
 
   // F[] starts at zero; every tile leaves it at zero again (the output pass
   // clears the words the walks touched)
-  for (int c = threadIdx.x; c < (int)(TT * sizeof(FV) / 16); c += NTF)
-    reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
+  for (int c = threadIdx.x; c < TT / 4; c += NTF) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x == 0) misc[0] = 0;
 
   TileQueue tq(p.queue + 1, p.ntiles);
@@ -479,7 +472,7 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
     for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
-      typename std::conditional<WT, double, uint32_t>::type in = 0;
+      uint32_t in = 0;
       bool any = false;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
@@ -488,18 +481,13 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
         const int64_t gi = g.i0 + li, gj = g.j0 + lj;
         if (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) continue;
         if (d.dir[gi * d.lddir + gj] != opposite(k)) continue;
-        in += fin_in(xval[global_slot(d, gi, gj, T)]);
+        in += xval[global_slot(d, gi, gj, T)];
         any = true;
       }
       if (any) {
         const int r = atomicAdd(&misc[0], 1);
         rcell[r] = (uint16_t)(i * T + j);
-        if constexpr (WT) {
-          const float hi = __double2float_rn((double)in);
-          rin[r] = FV{hi, __double2float_rn((double)in - (double)hi)};
-        } else {
-          rin[r] = in;
-        }
+        rin[r] = in;
       }
     }
     __syncthreads();
@@ -508,9 +496,9 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
     // T^2 cells; the bound only matters for a field with a cycle, which the
     // first pass reports)
     for (int r = threadIdx.x; r < nrec; r += NTF) {
-      const FV in = rin[r];
+      const uint32_t in = rin[r];
       int c = rcell[r], i = c / T, j = c & (T - 1);
-      fin_add(F, c, in);
+      atomicAdd(&F[c], in);
       for (int step = 0; step < TT; step++) {
         const int k = code[c];
         if (k >= 8) break;
@@ -518,60 +506,187 @@ __global__ void __launch_bounds__(NTF, WT ? 5 : 8) k_fin_unit(DemTable dt, Pipe 
         j += code_dj(k);
         if ((unsigned)i >= (unsigned)g.th || (unsigned)j >= (unsigned)g.tw) break;
         c = i * T + j;
-        fin_add(F, c, in);
+        atomicAdd(&F[c], in);
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) misc[0] = 0;
     // A += F where F is nonzero; touched words go back to zero
-    if (!WT) {
-      uint32_t* F32 = reinterpret_cast<uint32_t*>(F);
-      for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-        const uint4 f = reinterpret_cast<const uint4*>(F32)[q];
-        if (!(f.x | f.y | f.z | f.w)) continue;
-        reinterpret_cast<uint4*>(F32)[q] = make_uint4(0, 0, 0, 0);
-        const int c = q * 4, i = c / T, j = c - i * T;
-        if (i >= g.th) continue;
-        uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
-        if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-          uint4 a = *reinterpret_cast<uint4*>(dst);
-          a.x += f.x;
-          a.y += f.y;
-          a.z += f.z;
-          a.w += f.w;
-          *reinterpret_cast<uint4*>(dst) = a;
-        } else {
-          const uint32_t fv[4] = {f.x, f.y, f.z, f.w};
+    for (int q = threadIdx.x; q < TT / 4; q += NTF) {
+      const uint4 f = reinterpret_cast<const uint4*>(F)[q];
+      if (!(f.x | f.y | f.z | f.w)) continue;
+      reinterpret_cast<uint4*>(F)[q] = make_uint4(0, 0, 0, 0);
+      const int c = q * 4, i = c / T, j = c - i * T;
+      if (i >= g.th) continue;
+      uint32_t* dst = static_cast<uint32_t*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
+      if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        uint4 a = *reinterpret_cast<uint4*>(dst);
+        a.x += f.x;
+        a.y += f.y;
+        a.z += f.z;
+        a.w += f.w;
+        *reinterpret_cast<uint4*>(dst) = a;
+      } else {
+        const uint32_t fv[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (j + k < g.tw && fv[k]) dst[k] += fv[k];
-        }
+        for (int k = 0; k < 4; k++)
+          if (j + k < g.tw && fv[k]) dst[k] += fv[k];
       }
-    } else {
-      float4* F4 = reinterpret_cast<float4*>(F);
+    }
+  }
+}
+
+// Algorithms 7-8 for weighted areas, on the same sub-forest (the receivers'
+// in-tile paths), without floating-point atomics (they are not native in
+// shared memory and converging paths would retry them): a marking walk from
+// each receiver counts, per reached cell, its inputs that carry inflow and
+// which neighbours they are, stopping where the cell was already reached or
+// is a receiver itself; the receivers with no such input are noted; then the
+// inflow is propagated in dependency order, each cell's float-float F being
+// its own inflow plus its inputs' F pulled in N..NW order (deterministic),
+// published behind block fences as in the tile pass.  A = fp32(A + F).
+template <int T>
+__global__ void __launch_bounds__(NTF, 4) k_fin_w(DemTable dt, Pipe p) {
+  using L = FinWLayout<T>;
+  extern __shared__ __align__(16) unsigned char sm[];
+  ff* F = reinterpret_cast<ff*>(sm + L::off_f);
+  uint32_t* mk = reinterpret_cast<uint32_t*>(sm + L::off_mk);
+  uint8_t* code = sm + L::off_code;
+  uint16_t* rcell = reinterpret_cast<uint16_t*>(sm + L::off_rcell);
+  int* misc = reinterpret_cast<int*>(sm + L::off_misc);
+  const ff* xval = static_cast<const ff*>(p.S);
+  constexpr int TT = T * T;
+  constexpr int RPT = (4 * T + NTF - 1) / NTF;  // receivers per thread at most
+  // in-tile down-slope cell of c, or -1
+  auto down = [&](int c, const TileGeo& g) -> int {
+    const int k = code[c];
+    if (k >= 8) return -1;
+    const int i = c / T + code_di(k), j = (c & (T - 1)) + code_dj(k);
+    return ((unsigned)i < (unsigned)g.th && (unsigned)j < (unsigned)g.tw) ? i * T + j : -1;
+  };
+
+  // F[] and mk[] (adjacent) start at zero; every tile leaves them at zero
+  for (int c = threadIdx.x; c < (int)(TT * (sizeof(ff) + 4) / 16); c += NTF)
+    reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
+  if (threadIdx.x == 0) misc[0] = 0;
+
+  TileQueue tq(p.queue + 1, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
+    const DemDesc d = dem_of(dt, t);
+    const TileGeo g = tile_geo(d, t - d.tile_base, T);
+    {
+      const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
       for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-        const float4 fa = F4[2 * q], fb = F4[2 * q + 1];  // {hi, lo} of four cells
-        const double f[4] = {(double)fa.x + (double)fa.y, (double)fa.z + (double)fa.w, (double)fb.x + (double)fb.y,
-                             (double)fb.z + (double)fb.w};
-        if (fa.x == 0.f && fa.y == 0.f && fa.z == 0.f && fa.w == 0.f && fb.x == 0.f && fb.y == 0.f && fb.z == 0.f &&
-            fb.w == 0.f)
-          continue;  // (raw parts: a {hi, lo} that cancels must still be cleared)
-        F4[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        F4[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         const int c = q * 4, i = c / T, j = c - i * T;
         if (i >= g.th) continue;
-        float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
-        if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-          float4 a = *reinterpret_cast<float4*>(dst);
-          float* av = reinterpret_cast<float*>(&a);
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (f[k] != 0.0) av[k] = __double2float_rn((double)av[k] + f[k]);
-          *reinterpret_cast<float4*>(dst) = a;
+        const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
+        uint32_t four = 0x08080808u;
+        if (vec) {
+          four = __ldg(reinterpret_cast<const unsigned int*>(src));
         } else {
 #pragma unroll
           for (int k = 0; k < 4; k++)
-            if (j + k < g.tw && f[k] != 0.0) dst[k] = __double2float_rn((double)dst[k] + f[k]);
+            if (j + k < g.tw) four = (four & ~(0xFFu << (8 * k))) | ((uint32_t)src[k] << (8 * k));
+        }
+        reinterpret_cast<uint32_t*>(code)[q] = four;
+      }
+    }
+    // Algorithm 7: receivers, their inflow in F, marked
+    for (int s = threadIdx.x; s < 4 * T; s += NTF) {
+      int i, j;
+      if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
+      ff in{0.0f, 0.0f};
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int li = i + code_di(k), lj = j + code_dj(k);
+        if (li >= 0 && lj >= 0 && li < g.th && lj < g.tw) continue;
+        const int64_t gi = g.i0 + li, gj = g.j0 + lj;
+        if (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) continue;
+        if (d.dir[gi * d.lddir + gj] != opposite(k)) continue;
+        in = ff_add(in, xval[global_slot(d, gi, gj, T)]);
+        any = true;
+      }
+      if (any) {
+        const int c = i * T + j;
+        rcell[atomicAdd(&misc[0], 1)] = (uint16_t)c;
+        F[c] = in;
+        mk[c] = MK_REC;
+      }
+    }
+    __syncthreads();
+    const int nrec = misc[0];
+    // marking walk (integer atomics only)
+    for (int r = threadIdx.x; r < nrec; r += NTF) {
+      int c = rcell[r];
+      for (int step = 0; step < TT; step++) {
+        const int n = down(c, g);
+        if (n < 0) break;
+        const uint32_t old = atomicAdd(&mk[n], MK_CNT1 | (1u << opposite(code[c])));
+        if (old & (0xFF00u | MK_REC)) break;  // reached before, or a receiver with a walk of its own
+        c = n;
+      }
+    }
+    __syncthreads();
+    // the receivers with no inflow-carrying input start the propagation; noted
+    // before any walk changes the counts
+    uint32_t starts = 0;
+#pragma unroll
+    for (int k = 0; k < RPT; k++) {
+      const int r = threadIdx.x + k * NTF;
+      if (r < nrec && ((mk[rcell[r]] >> 8) & 0xFFu) == 0u) starts |= 1u << k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) misc[0] = 0;
+#pragma unroll
+    for (int k = 0; k < RPT; k++) {
+      if (!((starts >> k) & 1u)) continue;
+      int c = rcell[threadIdx.x + k * NTF];
+      for (int step = 0; step < TT; step++) {
+        const int n = down(c, g);
+        if (n < 0) break;
+        __threadfence_block();  // F[c] before the arrival that publishes it
+        const uint32_t old = atomicSub(&mk[n], MK_CNT1);
+        if (((old >> 8) & 0xFFu) != 1u) break;
+        __threadfence_block();
+        ff v = F[n];  // its own inflow (receivers) or zero
+        for (uint32_t m = old & 0xFFu; m; m &= m - 1) v = ff_add(v, F[n + toff_tab<T>(__ffs(m) - 1)]);
+        F[n] = v;
+        c = n;
+      }
+    }
+    __syncthreads();
+    // A = fp32(A + F) on the cells inflow reached (float-float add, fp32
+    // arithmetic only: fp64 is slow on this GPU); F and marks go back to zero
+    float4* F4 = reinterpret_cast<float4*>(F);
+    for (int q = threadIdx.x; q < TT / 4; q += NTF) {
+      const uint4 m4 = reinterpret_cast<const uint4*>(mk)[q];
+      if (!(m4.x | m4.y | m4.z | m4.w)) continue;  // F is nonzero only on marked cells
+      reinterpret_cast<uint4*>(mk)[q] = make_uint4(0, 0, 0, 0);
+      const float4 fa = F4[2 * q], fb = F4[2 * q + 1];  // {hi, lo} of four cells
+      F4[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      F4[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int c = q * 4, i = c / T, j = c - i * T;
+      if (i >= g.th) continue;
+      const ff f[4] = {ff{fa.x, fa.y}, ff{fa.z, fa.w}, ff{fb.x, fb.y}, ff{fb.z, fb.w}};
+      const bool on[4] = {(m4.x & 0x1FFFFu) != 0u, (m4.y & 0x1FFFFu) != 0u, (m4.z & 0x1FFFFu) != 0u,
+                          (m4.w & 0x1FFFFu) != 0u};
+      float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
+      if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        float4 a = *reinterpret_cast<float4*>(dst);
+        float* av = reinterpret_cast<float*>(&a);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const ff r = ff_add(ff{av[k], 0.0f}, f[k]);
+          if (on[k]) av[k] = __fadd_rn(r.hi, r.lo);
+        }
+        *reinterpret_cast<float4*>(dst) = a;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          if (j + k >= g.tw || !on[k]) continue;
+          const ff r = ff_add(ff{dst[k], 0.0f}, f[k]);
+          dst[k] = __fadd_rn(r.hi, r.lo);
         }
       }
     }
@@ -604,8 +719,8 @@ static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, cudaStrea
 
 template <int T, bool WT>
 static cudaError_t launch_down_unit_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
-  const size_t bytes = FinLayout<T, WT>::bytes;
-  auto k = k_fin_unit<T, WT>;
+  const size_t bytes = WT ? FinWLayout<T>::bytes : FinLayout<T>::bytes;
+  auto k = WT ? k_fin_w<T> : k_fin_unit<T>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k<<<persistent_grid_u(k, NTF, bytes, p.ntiles), NTF, bytes, s>>>(dt, p);
