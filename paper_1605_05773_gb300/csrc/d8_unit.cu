@@ -36,8 +36,17 @@
 namespace d8 {
 namespace unit {
 
+#ifndef D8_WNT
+#define D8_WNT 256
+#endif
 constexpr int NTU = 128;  // threads per tile block (4 warps)
-constexpr int NWU = NTU / 32;
+// Threads per tile of the first pass: a weighted 64 x 64 tile needs 57 KB of
+// shared memory (3 per SM), so weighted tiles of 64 and up get 8 warps each
+// to keep enough warps resident; 32 x 32 tiles have too few cells for that.
+template <int T, bool WT>
+struct UpThreads {
+  static constexpr int N = (WT && T >= 64) ? D8_WNT : NTU;
+};
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int RING = 64;  // pending sources per warp (a power of two > 63)
 constexpr int NTF = 256;  // threads per finalising block (its walks are few; the loads want warps)
@@ -136,8 +145,8 @@ struct UpLayout {
   static constexpr size_t TT = (size_t)T * T;
   static constexpr size_t off_word = 0;
   static constexpr size_t off_seg = TT * 4;
-  static constexpr size_t off_ring = off_seg + TT * 2;  // NWU rings of RING entries
-  static constexpr size_t off_misc = off_ring + (size_t)NWU * RING * 2;
+  static constexpr size_t off_ring = off_seg + TT * 2;  // one ring of RING entries per warp
+  static constexpr size_t off_misc = off_ring + (size_t)(UpThreads<T, WT>::N / 32) * RING * 2;
   static constexpr size_t off_val = off_misc + 64;  // weighted: float-float value per cell
   static constexpr size_t bytes = off_val + (WT ? TT * sizeof(ff) : 0);
 };
@@ -175,13 +184,14 @@ constexpr uint32_t MK_CNT1 = 1u << 8, MK_REC = 1u << 16;
 template <int T, bool WT>
 __device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const TileGeo& g, uint32_t* word, ff* val,
                                                     uint32_t* status) {
-  constexpr int NQ = T * T / 4 / NTU;  // four-cell groups per thread
+  constexpr int NT = UpThreads<T, WT>::N;
+  constexpr int NQ = T * T / 4 / NT;  // four-cell groups per thread
   const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
   // issue every load of this thread before using any (hides the memory latency)
   uint32_t fours[NQ];
 #pragma unroll
   for (int r = 0; r < NQ; r++) {
-    const int c = (threadIdx.x + r * NTU) * 4, i = c / T, j = c - i * T;
+    const int c = (threadIdx.x + r * NT) * 4, i = c / T, j = c - i * T;
     fours[r] = 0;
     if (i < g.th) {
       const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
@@ -196,7 +206,7 @@ __device__ __forceinline__ void tile_codes_from_dir(const DemDesc& d, const Tile
   }
 #pragma unroll
   for (int r = 0; r < NQ; r++) {
-    const int q = threadIdx.x + r * NTU;
+    const int q = threadIdx.x + r * NT;
     const int c = q * 4, i = c / T, j = c - i * T;
     if (i >= g.th) continue;
     const uint32_t four = fours[r];
@@ -241,7 +251,7 @@ __device__ __forceinline__ void store_counts(const DemDesc& d, const TileGeo& g,
 // Weighted: A[tile] = the in-tile areas held in val[], rounded to fp32.
 template <int T>
 __device__ __forceinline__ void store_areas(const DemDesc& d, const TileGeo& g, const ff* val) {
-  for (int q = threadIdx.x; q < T * T / 4; q += NTU) {
+  for (int q = threadIdx.x; q < T * T / 4; q += UpThreads<T, true>::N) {
     const int c = q * 4, i = c / T, j = c - i * T;
     if (i >= g.th) continue;
     float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
@@ -268,7 +278,8 @@ __device__ __forceinline__ ff pull_value(const ff* val, int c, uint32_t w) {
 }
 
 template <int T, bool WT>
-__global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p) {
+__global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p) {
+  constexpr int NT = UpThreads<T, WT>::N;
   using L = UpLayout<T, WT>;
   using W = WL<T>;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     uint4* w4 = reinterpret_cast<uint4*>(word);
-    for (int c = threadIdx.x; c < TT / 4; c += NTU) w4[c] = make_uint4(0, 0, 0, 0);
+    for (int c = threadIdx.x; c < TT / 4; c += NT) w4[c] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) misc[0] = 0;
     __syncthreads();
     tile_codes_from_dir<T, WT>(d, g, word, val, p.status);  // Algorithm 1
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p
     // Algorithm 2.  Every lane walks down-slope from a source while it is the
     // last input to arrive at the next cell; a lane whose walk stopped takes
     // the warp's next pending source.  Pending sources sit in a per-warp ring,
-    // refilled by scanning the warp's own cells (c = lane + 32 w + NTU r) a
+    // refilled by scanning the warp's own cells (c = lane + 32 w + NT r) a
     // row at a time with a ballot.  A source is a cell with count 1 and no
     // input left (an absent cell of a ragged tile has count 0); the word of a
     // cell whose last input has arrived holds count >= 2, so a scan running
@@ -308,8 +319,8 @@ __global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p
       uint32_t acc = 0, wv = 0;
       ff v{0.0f, 0.0f};
       for (;;) {
-        while (tail - head < 32 && r < TT / NTU) {  // at most RING - 1 pending
-          const int c = threadIdx.x + r * NTU;
+        while (tail - head < 32 && r < TT / NT) {  // at most RING - 1 pending
+          const int c = threadIdx.x + r * NT;
           const bool src = WT ? (word[c] & W_SRC_W) == W_PRES : (word[c] & W::SRC_MASK) == 1u;
           const unsigned m = __ballot_sync(FULL, src);
           if (src) ring[(tail + __popc(m & lt)) & (RING - 1)] = (uint16_t)c;
@@ -375,7 +386,7 @@ __global__ void __launch_bounds__(NTU, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p
       store_counts<T>(d, g, word);
     // perimeter summary: the exit of each perimeter cell's in-tile path, by a
     // chase over segment records (resolved records are written back)
-    for (int s = threadIdx.x; s < 4 * T; s += NTU) {
+    for (int s = threadIdx.x; s < 4 * T; s += NT) {
       int i, j;
       uint16_t pe = PEX_TERM;
       uint32_t pv = 0;
@@ -713,7 +724,7 @@ static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, cudaStrea
   auto k = k_up_unit<T, WT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k<<<persistent_grid_u(k, NTU, bytes, p.ntiles), NTU, bytes, s>>>(dt, p);
+  k<<<persistent_grid_u(k, UpThreads<T, WT>::N, bytes, p.ntiles), UpThreads<T, WT>::N, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
