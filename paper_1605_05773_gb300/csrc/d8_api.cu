@@ -184,7 +184,7 @@ HShape hier_shape(int T, int n, const int64_t* H, const int64_t* W) {
   return hs;
 }
 
-// vb: bytes per level value (4 for unit counts, 8 for the weighted doubles)
+// vb: bytes per level value (4 for unit counts, 8 for weighted float-float)
 size_t hier_bytes(const HShape& hs, size_t vb) {
   size_t b = 0;
   for (int l = 1; l <= hs.nlev; l++) {
@@ -198,13 +198,10 @@ size_t hier_bytes(const HShape& hs, size_t vb) {
 }
 
 // Carve the level arrays; level 0 takes the tile pipeline's arrays.  `dts`
-// holds each level's DEM table (filled by the caller).  Weighted: the tiles'
-// float-float pval is level 0's input, its double fin lives in the pipe's
-// second value buffer (unused by this combine) and is rounded into Pipe::S.
+// holds each level's DEM table (filled by the caller).
 HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dts, bool weighted) {
   HPlan hp{};
   hp.weighted = weighted;
-  hp.ff_out = weighted ? p.S : nullptr;
   hp.nlev = hs.nlev;
   hp.need_top = hs.need_top;
   hp.status = p.status;
@@ -213,7 +210,7 @@ HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dt
   hp.lev[0].dt = dts[0];
   hp.lev[0].pex = p.pex;
   hp.lev[0].pval = p.pval;
-  hp.lev[0].fin = weighted ? p.S2 : p.S;
+  hp.lev[0].fin = p.S;
   const size_t vb = weighted ? 8 : 4;
   char* q = static_cast<char*>(base);
   for (int l = 1; l <= hs.nlev; l++) {

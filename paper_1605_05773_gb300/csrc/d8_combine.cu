@@ -17,11 +17,8 @@
 // at level 0 that is the final area of every tile exit, which the tiles'
 // finalising pass reads.
 //
-// Unit counts travel as uint32.  Weighted areas travel as doubles above the
-// tiles (shared-memory and global fp64 atomic adds; the level sums carry more
-// precision than the tiles' float-float values they start from), and the
-// level-0 results are rounded back to float-float (hi = fp32 nearest, lo =
-// fp32 nearest of the remainder) for the finalising pass.
+// Unit counts travel as uint32, weighted areas as float-float values (fp32
+// arithmetic throughout, with compensated atomic adds).
 #include "d8_device.cuh"
 
 namespace d8 {
@@ -47,10 +44,27 @@ struct GroupLayout {
 
 __device__ __forceinline__ DemDesc dem_by_index(const DemTable& t, int k) { return t.ndem == 1 ? t.one : t.table[k]; }
 
-// a child's stored value in the accumulation type (float-float -> double is exact)
-__device__ __forceinline__ uint32_t to_acc(uint32_t v, uint32_t) { return v; }
-__device__ __forceinline__ double to_acc(double v, double) { return v; }
-__device__ __forceinline__ double to_acc(ff v, double) { return (double)v.hi + (double)v.lo; }
+// Value arithmetic: uint32 counts, or float-float areas.  A float-float
+// atomic add (fp32 atomics exist in shared and global memory; fp64 arithmetic
+// is slow on this GPU) adds the high part with an atomic that returns the old
+// value, takes that add's exact rounding error by TwoSum and adds it with the
+// low part into the low word: only the rounding of the low word's own sums is
+// lost.  The parts are not renormalised between adds, which float-float
+// addition tolerates.
+__device__ __forceinline__ uint32_t vadd(uint32_t a, uint32_t b) { return a + b; }
+__device__ __forceinline__ ff vadd(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ void vatomic_add(uint32_t* p, uint32_t x) { atomicAdd(p, x); }
+__device__ __forceinline__ void vatomic_add(ff* p, ff x) {
+  const float old = atomicAdd(&p->hi, x.hi);
+  const float s = __fadd_rn(old, x.hi);
+  const float bv = __fsub_rn(s, old);
+  const float err = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bv)), __fsub_rn(x.hi, bv));
+  atomicAdd(&p->lo, __fadd_rn(err, x.lo));
+}
+__device__ __forceinline__ uint32_t vload_volatile(const uint32_t* p) { return *(volatile const uint32_t*)p; }
+__device__ __forceinline__ ff vload_volatile(const ff* p) {
+  return ff{*(volatile const float*)&p->hi, *(volatile const float*)&p->lo};
+}
 
 struct UnitGeo {
   int64_t i0, j0;
@@ -84,12 +98,12 @@ __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint1
     const int lt = n / (4 * S), s = n - lt * (4 * S);
     const int64_t cy = gy * G + lt / G, cx = gx * G + lt % G;
     uint16_t pe = PEX_TERM;
-    V v = 0;
+    V v{};
     if (cy < cd.nty && cx < cd.ntx) {
       const int64_t cu = cd.tile_base + cy * cd.ntx + cx;
       pe = cpex[cu * (4 * S) + s];
       if (pe & PEX_EXIT) {
-        v = to_acc(cpval[cu * (4 * S) + s], V());
+        v = cpval[cu * (4 * S) + s];
         exits++;
       }
     }
@@ -154,7 +168,7 @@ __device__ int group_walk(uint16_t* spx, V* val, uint32_t* pd, uint16_t* srcl) {
   }
   __syncthreads();
   int done = 0, head = 0, cur = -1;
-  V v = 0;
+  V v{};
   const unsigned lt = (1u << lane) - 1u;
   for (;;) {
     if (head < n) {
@@ -175,13 +189,13 @@ __device__ int group_walk(uint16_t* spx, V* val, uint32_t* pd, uint16_t* srcl) {
         cur = -1;
         continue;
       }
-      atomicAdd(&val[p], v);
+      vatomic_add(&val[p], v);
       __threadfence_block();
       const uint32_t old = atomicSub(&pd[p], 1u);
       if (pd_deg(old) == 1u) {
         __threadfence_block();
         cur = p;
-        v = *(volatile V*)&val[p];
+        v = vload_volatile(&val[p]);
         done++;
       } else {
         cur = -1;
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(NTG) k_group_up(DemTable cdt, DemTable gdt, co
     for (int gs = threadIdx.x; gs < 4 * GS; gs += NTG) {
       int ci, cj;
       uint16_t gpe = PEX_TERM;
-      V gv = 0;
+      V gv{};
       if (slot_cell(gs, gg.h, gg.w, GS, ci, cj)) {
         const int a = ci / S, b = cj / S;
         const UnitGeo cu = unit_geo(cd, gy * G + a, gx * G + b, S);
@@ -290,7 +304,7 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
       int ci, cj;
       if (!slot_cell(gs, gg.h, gg.w, GS, ci, cj)) continue;
       const int64_t gi = gg.i0 + ci, gj = gg.j0 + cj;
-      V in = 0;
+      V in{};
       bool any = false;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
@@ -299,7 +313,7 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
         const int64_t ni = gi + code_di(k), nj = gj + code_dj(k);
         if (ni < 0 || nj < 0 || ni >= gd.H || nj >= gd.W) continue;
         if (gd.dir[ni * gd.lddir + nj] != opposite(k)) continue;
-        in += gfin[global_slot(gd, ni, nj, GS)];
+        in = vadd(in, gfin[global_slot(gd, ni, nj, GS)]);
         any = true;
       }
       if (!any) continue;
@@ -309,9 +323,9 @@ __global__ void __launch_bounds__(NTG) k_group_down(DemTable cdt, DemTable gdt, 
       const int n0 = lt * (4 * S) + slot_of(ci - a * S, cj - b * S, cu.h, cu.w, S);
       const uint16_t pe = spx[n0];
       if (pe & PEX_EXIT)
-        atomicAdd(&val[n0], in);
+        vatomic_add(&val[n0], in);
       else if (pe != PEX_TERM)
-        atomicAdd(&val[lt * (4 * S) + pe], in);
+        vatomic_add(&val[lt * (4 * S) + pe], in);
     }
     __syncthreads();
     group_walk<S, G, V>(spx, val, pd, srcl);
@@ -350,7 +364,7 @@ __global__ void k_top_init(DemTable dt, const uint16_t* pex, const CV* pval, V* 
       else if (pey != PEX_TERM)
         pr = (uint32_t)((y / (4 * S)) * (4 * S) + pey);
       if (pr != ROOT) atomicAdd(&deg[pr], 1u);
-      fin[g] = to_acc(pval[g], V());
+      fin[g] = pval[g];
     }
     par[g] = pr;
   }
@@ -388,27 +402,16 @@ __global__ void k_top_walk(const uint32_t* par, V* fin, uint32_t* deg, const uin
     for (;;) {
       const uint32_t p = par[x];
       if (p == ROOT) break;
-      atomicAdd(&fin[p], v);
+      vatomic_add(&fin[p], v);
       __threadfence();
       if (atomicSub(&deg[p], 1u) != 1u) break;
       __threadfence();
       x = p;
-      v = *(volatile V*)&fin[p];
+      v = vload_volatile(&fin[p]);
       done++;
     }
   }
   if (done) atomicAdd(&counters[2], done);
-}
-
-// weighted: level-0 final values at exits, double -> float-float
-__global__ void k_round_ff(const uint16_t* pex, const double* fin, ff* out, int64_t nslots) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
-    if (!(pex[g] & PEX_EXIT)) continue;
-    const double v = fin[g];
-    const float hi = __double2float_rn(v);
-    out[g] = ff{hi, __double2float_rn(v - (double)hi)};
-  }
 }
 
 __global__ void k_top_check(const uint32_t* counters, uint32_t* status) {
@@ -560,19 +563,7 @@ static cudaError_t combine_hier_t(const HPlan& hp, cudaStream_t s, int* nlaunch)
 
 cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch) {
   if (!hp.weighted) return cmb::combine_hier_t<uint32_t, uint32_t>(hp, s, nlaunch);
-  cudaError_t e = cmb::combine_hier_t<double, ff>(hp, s, nlaunch);
-  if (e != cudaSuccess) return e;
-  const HLevel& l0 = hp.lev[0];
-  const int64_t ns = l0.nunits * 4 * l0.S;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t b = (ns + 255) / 256;
-  if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
-  cmb::k_round_ff<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(l0.pex, static_cast<const double*>(l0.fin),
-                                                            static_cast<ff*>(hp.ff_out), ns);
-  ++*nlaunch;
-  return cudaGetLastError();
+  return cmb::combine_hier_t<ff, ff>(hp, s, nlaunch);
 }
 
 }  // namespace d8

@@ -74,18 +74,15 @@ cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, i
 // units.  Every level has per-unit perimeter summaries of the same format:
 // per perimeter slot the exit code (pex), the in-unit value at exits (pval)
 // and, after the down sweep, the final value at exits (fin).  Values are
-// uint32 counts (unit weights) or, for weighted areas, doubles on every level
-// except the tiles' own pval (float-float, from the weighted tile pass); the
-// level-0 fin of a weighted run is a double array rounded to float-float for
-// the finalising pass at the end.
+// uint32 counts (unit weights) or float-float areas (weighted).
 constexpr int HMAX = 8;
 struct HLevel {
   int S;            // unit side in cells
   int64_t nunits;   // units over all DEMs
   DemTable dt;      // per-DEM unit grid (ntx, nty, tile_base) at this level
   uint16_t* pex;
-  void* pval;       // uint32 / double (level 0 weighted: ff)
-  void* fin;        // uint32 / double
+  void* pval;       // uint32 / ff
+  void* fin;        // uint32 / ff
 };
 struct HTop {  // the top level's queue-method solve in global memory
   uint32_t* par;
@@ -95,8 +92,7 @@ struct HTop {  // the top level's queue-method solve in global memory
   uint32_t* status;
 };
 struct HPlan {
-  bool weighted;  // double values above the tiles; level-0 fin rounded into ff_out
-  void* ff_out;   // weighted: the tiles' float-float final values at exits (Pipe::S)
+  bool weighted;  // float-float values instead of uint32 counts
   int nlev;  // group levels 1..nlev above the tiles
   HLevel lev[HMAX];
   bool need_top;

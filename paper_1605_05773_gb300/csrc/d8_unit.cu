@@ -36,16 +36,14 @@
 namespace d8 {
 namespace unit {
 
-#ifndef D8_WNT
-#define D8_WNT 256
-#endif
 constexpr int NTU = 128;  // threads per tile block (4 warps)
+constexpr int NTW = 256;  // threads per weighted tile block of side 64 and up (8 warps)
 // Threads per tile of the first pass: a weighted 64 x 64 tile needs 57 KB of
 // shared memory (3 per SM), so weighted tiles of 64 and up get 8 warps each
 // to keep enough warps resident; 32 x 32 tiles have too few cells for that.
 template <int T, bool WT>
 struct UpThreads {
-  static constexpr int N = (WT && T >= 64) ? D8_WNT : NTU;
+  static constexpr int N = (WT && T >= 64) ? NTW : NTU;
 };
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int RING = 64;  // pending sources per warp (a power of two > 63)
