@@ -515,9 +515,12 @@ d8_status d8_accumulate_backward(d8_ctx* c, const uint8_t* dir, int64_t H, int64
   d.ldA = lddw;
   const int64_t ntiles = d.ntx * d.nty;
   if (!slots_fit(ntiles, T)) return D8_ERR_SHAPE;
-  d8_status st = ensure_ws(c, pipe_bytes(ntiles, T, 8));
+  // the pipe, then one uint16 per cell: the slot of the cell's tile exit
+  const size_t pb = align256(pipe_bytes(ntiles, T, 8));
+  d8_status st = ensure_ws(c, pb + align256((size_t)H * (size_t)W * 2));
   if (st != D8_OK) return st;
   Pipe p = carve_pipe(c->ws, ntiles, T, 8, c->status);
+  p.xid = reinterpret_cast<uint16_t*>(static_cast<char*>(c->ws) + pb);
   DemTable dt = single(d);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);

@@ -10,7 +10,10 @@
 //              H(x) = (path sum of y inside its tile) + H(exit of y); a path
 //              sum over the exit forest, found by pointer jumping (gathers
 //              only, so deterministic).
-//  k_bwd_down  per tile: dw(q) = in-tile path sum of q + H(exit of q).
+//              It also writes every cell's in-tile path sum to dw and the
+//              slot of its tile exit to a per-cell array.
+//  k_bwd_fix   streaming: dw(q) += H(exit of q) for the cells whose path
+//              leaves their tile (float-float add of the rounded path sum).
 #include "d8_device.cuh"
 
 namespace d8 {
@@ -130,6 +133,16 @@ __global__ void __launch_bounds__(NT) k_bwd_up(DemTable dt, Pipe p) {
       p.pex[t * (4 * T) + s] = pe;
       pval[t * (4 * T) + s] = v;
     }
+    // every cell: its in-tile path sum (to dw) and its exit's slot
+    for (int c = threadIdx.x; c < TT; c += NT) {
+      const int i = c / T, j = c - i * T;
+      if (i >= g.th || j >= g.tw) continue;
+      const ff v = gs[b * TT + c];
+      const int e = en[b * TT + c];
+      const int64_t gi = g.i0 + i, gj = g.j0 + j;
+      static_cast<float*>(d.A)[gi * d.ldA + gj] = __fadd_rn(v.hi, v.lo);
+      p.xid[gi * d.W + gj] = (cl[e] & CL_EXIT) ? (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T) : NO_EXIT;
+    }
     __syncthreads();
   }
 }
@@ -196,30 +209,50 @@ __global__ void k_bpj_check(Pipe p, int R) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && p.flags[R] != 0u) set_status(p.status, D8_ERR_CYCLE);
 }
 
-template <int T>
-__global__ void __launch_bounds__(NT) k_bwd_down(DemTable dt, Pipe p) {
-  using L = BwdLayout<T>;
-  extern __shared__ __align__(16) unsigned char sm[];
-  ff* gs = reinterpret_cast<ff*>(sm + L::off_gs);
-  uint16_t* en = reinterpret_cast<uint16_t*>(sm + L::off_en);
-  const uint8_t* cl = sm + L::off_cl;
+// dw(q) = (in-tile path sum of q, already in dw) + H(exit of q); four
+// consecutive cells of a row per thread (8-byte exit-slot loads, 16-byte dw
+// accesses) when the row layout allows, else one cell per thread
+template <int T, bool VEC>
+__global__ void k_bwd_fix(DemTable dt, Pipe p) {
+  const DemDesc d = dt.one;
   const uint32_t last = *(volatile uint32_t*)&p.flags[MAX_ROUNDS + 1];
   const ff* H = static_cast<const ff*>((last & 1) ? p.S2 : p.S);
-  constexpr int TT = T * T;
-  TileQueue tq(p.queue + 3, p.ntiles);
-  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
-    const DemDesc d = dem_of(dt, t);
-    const TileGeo g = tile_geo(d, t - d.tile_base, T);
-    const int b = tile_path_sums<T>(d, g, sm, p.status);
-    for (int c = threadIdx.x; c < TT; c += NT) {
-      const int i = c / T, j = c - i * T;
-      if (i >= g.th || j >= g.tw) continue;
-      ff v = gs[b * TT + c];
-      const int e = en[b * TT + c];
-      if (cl[e] & CL_EXIT) v = ff_add(v, H[t * (4 * T) + slot_of(e / T, e % T, g.th, g.tw, T)]);
-      static_cast<float*>(d.A)[(g.i0 + i) * d.ldA + g.j0 + j] = __fadd_rn(v.hi, v.lo);
+  constexpr int V = VEC ? 4 : 1;
+  const int64_t wq = d.W / V;  // groups per row
+  const int64_t n = d.H * wq;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const int64_t gi = k / wq, gj = (k - gi * wq) * V;
+    uint16_t e[V];
+    if (VEC) {
+      const uint2 e4 = *reinterpret_cast<const uint2*>(p.xid + gi * d.W + gj);
+      e[0] = (uint16_t)e4.x;
+      e[V > 1 ? 1 : 0] = (uint16_t)(e4.x >> 16);
+      e[V > 2 ? 2 : 0] = (uint16_t)e4.y;
+      e[V > 3 ? 3 : 0] = (uint16_t)(e4.y >> 16);
+    } else {
+      e[0] = p.xid[gi * d.W + gj];
     }
-    __syncthreads();
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < V; u++) any |= e[u] != NO_EXIT;
+    if (!any) continue;
+    float* dst = static_cast<float*>(d.A) + gi * d.ldA + gj;
+    const int64_t trow = (gi / T) * d.ntx;
+    if (VEC) {
+      float4 a = *reinterpret_cast<float4*>(dst);
+      float* av = reinterpret_cast<float*>(&a);
+#pragma unroll
+      for (int u = 0; u < V; u++) {
+        if (e[u] == NO_EXIT) continue;
+        const ff v = ff_add(ff{av[u], 0.0f}, H[(trow + (gj + u) / T) * (4 * T) + e[u]]);
+        av[u] = __fadd_rn(v.hi, v.lo);
+      }
+      *reinterpret_cast<float4*>(dst) = a;
+    } else {
+      const ff v = ff_add(ff{*dst, 0.0f}, H[(trow + gj / T) * (4 * T) + e[0]]);
+      *dst = __fadd_rn(v.hi, v.lo);
+    }
   }
 }
 
@@ -259,12 +292,20 @@ static cudaError_t launch_bwd_up_t(const DemTable& dt, const Pipe& p, cudaStream
 }
 
 template <int T>
-static cudaError_t launch_bwd_down_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
-  const size_t bytes = BwdLayout<T>::bytes;
-  if (bytes > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_bwd_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  k_bwd_down<T><<<persistent_grid_b(k_bwd_down<T>, bytes, p.ntiles), NT, bytes, s>>>(dt, p);
+static cudaError_t launch_bwd_fix_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
+  const DemDesc& d = dt.one;
+  const bool vec = d.W % 4 == 0 && d.ldA % 4 == 0 && (reinterpret_cast<uintptr_t>(d.A) & 15u) == 0;
+  const int64_t n = d.H * (vec ? d.W / 4 : d.W);
+  int64_t b = (n + 255) / 256;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (b > (int64_t)sms * 32) b = (int64_t)sms * 32;
+  if (b < 1) b = 1;
+  if (vec)
+    k_bwd_fix<T, true><<<(unsigned)b, 256, 0, s>>>(dt, p);
+  else
+    k_bwd_fix<T, false><<<(unsigned)b, 256, 0, s>>>(dt, p);
   return cudaGetLastError();
 }
 
@@ -304,8 +345,8 @@ cudaError_t launch_combine_bwd(const DemTable& dt, const Pipe& p, cudaStream_t s
 cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch) {
   ++*nlaunch;
   switch (p.T) {
-    case 32: return launch_bwd_down_t<32>(dt, p, s);
-    case 64: return launch_bwd_down_t<64>(dt, p, s);
+    case 32: return launch_bwd_fix_t<32>(dt, p, s);
+    case 64: return launch_bwd_fix_t<64>(dt, p, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -54,7 +54,9 @@ struct Pipe {
   uint32_t* flags;   // combine: per-round "still active" flags, MAX_ROUNDS+2
   uint32_t* status;  // device status word (OR of 1 << d8_status)
   uint32_t* queue;   // tile work-queue counters (one per stage)
+  uint16_t* xid;     // adjoint only: per cell (row-major, W per row) the slot of its tile exit, or NO_EXIT
 };
+constexpr uint16_t NO_EXIT = 0xFFFFu;
 
 // ---- launchers (d8_flowdir.cu / d8_fwd.cu / d8_bwd.cu) ---------------------
 // Each enqueues its kernels on `s` and adds the number of kernel launches it
