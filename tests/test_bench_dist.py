@@ -67,3 +67,27 @@ def test_reference_arm_under_torchrun_prints_one_line():
 
 if __name__ == "__main__":
     sys.exit(pytest.main([__file__, "-q"]))
+
+
+def test_measured_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
+    """bench.py quotes ncu traffic only while the kernel's source still has the
+    hash recorded with the capture."""
+    import hashlib
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src_dir = tmp_path / "paper_1605_05773_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (src_dir / "d8_unit.cu").write_text("// kernel v1\n")
+    (src_dir / "d8_flowdir.cu").write_text("// stencil v1\n")
+    sha = hashlib.sha1(b"// kernel v1\n").hexdigest()[:12]
+    (tmp_path / "profiles" / "tile_kernels_fractal_8192.md").write_text(
+        f"    kernel_source_sha1 d8_unit.cu {sha}\n    kernel_source_sha1 d8_flowdir.cu 000000000000\n"
+        "    scaled_traffic_bytes_per_cell tile_up 4.48\n    scaled_traffic_bytes_per_cell flowdir 4.79\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("tile_up") == 4.48
+    assert bench.measured_traffic("flowdir") is None  # hash differs: stale capture
+    (src_dir / "d8_unit.cu").write_text("// kernel v2\n")
+    assert bench.measured_traffic("tile_up") is None
