@@ -65,9 +65,6 @@ def test_reference_arm_under_torchrun_prints_one_line():
     assert j["cpu_baseline"]["kind"] == "oracle" and j["e2e"]["h2d_bytes_per_step"] == 0
 
 
-if __name__ == "__main__":
-    sys.exit(pytest.main([__file__, "-q"]))
-
 
 def test_measured_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
     """bench.py quotes ncu traffic only while the kernel's source still has the
@@ -91,3 +88,7 @@ def test_measured_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypa
     assert bench.measured_traffic("flowdir") is None  # hash differs: stale capture
     (src_dir / "d8_unit.cu").write_text("// kernel v2\n")
     assert bench.measured_traffic("tile_up") is None
+
+
+if __name__ == "__main__":
+    sys.exit(pytest.main([__file__, "-q"]))
