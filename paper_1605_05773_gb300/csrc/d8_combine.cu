@@ -484,11 +484,13 @@ static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& 
 }  // namespace cmb
 
 // Level schedule: tiles of side T, then groups of G = 4 (from 32 or 64) or
-// G = 2 children, up to a group side of 1024 cells.
+// G = 2 children, up to a group side of 512 cells; the global queue solve
+// takes the rest.  (A 1024-cell level cost more than the longer top-level
+// chains it saves: measured at 8192^2 and 32768^2.)
 int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels) {
   int n = 0;
   int s = T;
-  while (n < max_levels && s < max_side && s < 1024) {
+  while (n < max_levels && s < max_side && s < 512) {
     const int g = (s <= 64) ? 4 : 2;
     S[n] = s;
     G[n] = g;
