@@ -370,24 +370,50 @@ __global__ void k_top_init(DemTable dt, const uint16_t* pex, const CV* pval, V* 
   }
 }
 
-__global__ void k_top_sources(const uint16_t* pex, const uint32_t* deg, uint32_t* list, uint32_t* counters,
-                              int64_t nslots) {
-  // one atomic per warp on each counter (they are shared by the whole grid)
-  const int lane = threadIdx.x & 31;
+// The sources (exits without children) listed, and the exits counted, with
+// one atomic per block on each grid-wide counter: a first pass counts this
+// thread's sources, a block scan gives each thread its offset inside the
+// block's range, and a second pass writes them (same slots, same order).
+__global__ void __launch_bounds__(256) k_top_sources(const uint16_t* pex, const uint32_t* deg, uint32_t* list,
+                                                     uint32_t* counters, int64_t nslots) {
+  __shared__ uint32_t sh[256];
+  __shared__ uint32_t sh_base;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < nslots; b += stride) {
-    const int64_t g = b + lane;
-    const bool ex = g < nslots && (pex[g] & PEX_EXIT);
-    const bool src = ex && deg[g] == 0u;
-    const unsigned ms = __ballot_sync(0xFFFFFFFFu, src), me = __ballot_sync(0xFFFFFFFFu, ex);
-    uint32_t base = 0;
-    if (lane == 0) {
-      if (ms) base = atomicAdd(&counters[0], (uint32_t)__popc(ms));
-      if (me) atomicAdd(&counters[1], (uint32_t)__popc(me));
-    }
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (src) list[base + __popc(ms & ((1u << lane) - 1u))] = (uint32_t)g;
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t nsrc = 0, nex = 0;
+  for (int64_t g = g0; g < nslots; g += stride) {
+    const bool ex = (pex[g] & PEX_EXIT) != 0;
+    nex += ex;
+    nsrc += ex && deg[g] == 0u;
   }
+  // block-wide inclusive scan of the source counts (Hillis-Steele)
+  sh[threadIdx.x] = nsrc;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const uint32_t add = threadIdx.x >= off ? sh[threadIdx.x - off] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += add;
+    __syncthreads();
+  }
+  const uint32_t block_src = sh[255];
+  uint32_t excl = sh[threadIdx.x] - nsrc;
+  __syncthreads();
+  // exits: reduce into sh[0] with a second scan-free pass
+  sh[threadIdx.x] = nex;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sh_base = block_src ? atomicAdd(&counters[0], block_src) : 0u;
+    if (sh[0]) atomicAdd(&counters[1], sh[0]);
+  }
+  __syncthreads();
+  uint32_t pos = sh_base + excl;
+  if (nsrc)
+    for (int64_t g = g0; g < nslots; g += stride)
+      if ((pex[g] & PEX_EXIT) && deg[g] == 0u) list[pos++] = (uint32_t)g;
 }
 
 // Algorithm 6 with global atomics: last-arriver walks up the exit forest.
