@@ -192,7 +192,7 @@ size_t hier_bytes(const HShape& hs, size_t vb) {
     b += align256(ns * 2) + 2 * align256(ns * vb);
   }
   const size_t nt = (size_t)hs.nunits[hs.nlev] * 4 * hs.S[hs.nlev];
-  if (hs.need_top) b += 3 * align256(nt * 4);
+  if (hs.need_top) b += 2 * align256(nt * 4) + align256(nt * 8);  // par, list; children counts (8 B: packed)
   b += align256(sizeof(uint32_t) * 64);
   return b;
 }
@@ -230,8 +230,8 @@ HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dt
   if (hs.need_top) {
     hp.top.par = reinterpret_cast<uint32_t*>(q);
     q += align256(nt * 4);
-    hp.top.deg = reinterpret_cast<uint32_t*>(q);
-    q += align256(nt * 4);
+    hp.top.deg = reinterpret_cast<uint32_t*>(q);  // 8 bytes per slot (unit counts pack value and count)
+    q += align256(nt * 8);
     hp.top.list = reinterpret_cast<uint32_t*>(q);
     q += align256(nt * 4);
   }

@@ -363,8 +363,16 @@ __global__ void k_top_init(DemTable dt, const uint16_t* pex, const CV* pval, V* 
         pr = (uint32_t)y;
       else if (pey != PEX_TERM)
         pr = (uint32_t)((y / (4 * S)) * (4 * S) + pey);
-      if (pr != ROOT) atomicAdd(&deg[pr], 1u);
-      fin[g] = pval[g];
+      if constexpr (std::is_same<V, uint32_t>::value) {
+        // unit counts: children left (high half) and value (low half) in one
+        // 64-bit word per node (zeroed before the launch)
+        unsigned long long* fd = reinterpret_cast<unsigned long long*>(deg);
+        if (pr != ROOT) atomicAdd(&fd[pr], 1ull << 32);
+        atomicAdd(&fd[g], (unsigned long long)pval[g]);
+      } else {
+        if (pr != ROOT) atomicAdd(&deg[pr], 1u);
+        fin[g] = pval[g];
+      }
     }
     par[g] = pr;
   }
@@ -374,8 +382,13 @@ __global__ void k_top_init(DemTable dt, const uint16_t* pex, const CV* pval, V* 
 // one atomic per block on each grid-wide counter: a first pass counts this
 // thread's sources, a block scan gives each thread its offset inside the
 // block's range, and a second pass writes them (same slots, same order).
+// (PK: children counts packed in the high half of 64-bit node words)
+template <bool PK>
 __global__ void __launch_bounds__(256) k_top_sources(const uint16_t* pex, const uint32_t* deg, uint32_t* list,
                                                      uint32_t* counters, int64_t nslots) {
+  auto childless = [&](int64_t g) {
+    return PK ? (reinterpret_cast<const unsigned long long*>(deg)[g] >> 32) == 0ull : deg[g] == 0u;
+  };
   __shared__ uint32_t sh[256];
   __shared__ uint32_t sh_base;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -384,7 +397,7 @@ __global__ void __launch_bounds__(256) k_top_sources(const uint16_t* pex, const 
   for (int64_t g = g0; g < nslots; g += stride) {
     const bool ex = (pex[g] & PEX_EXIT) != 0;
     nex += ex;
-    nsrc += ex && deg[g] == 0u;
+    nsrc += ex && childless(g);
   }
   // block-wide inclusive scan of the source counts (Hillis-Steele)
   sh[threadIdx.x] = nsrc;
@@ -413,28 +426,49 @@ __global__ void __launch_bounds__(256) k_top_sources(const uint16_t* pex, const 
   uint32_t pos = sh_base + excl;
   if (nsrc)
     for (int64_t g = g0; g < nslots; g += stride)
-      if ((pex[g] & PEX_EXIT) && deg[g] == 0u) list[pos++] = (uint32_t)g;
+      if ((pex[g] & PEX_EXIT) && childless(g)) list[pos++] = (uint32_t)g;
 }
 
 // Algorithm 6 with global atomics: last-arriver walks up the exit forest.
+// Unit counts: one packed 64-bit atomic per step delivers the value and tells
+// the last child (no fences); each finished node stores its value for the
+// down sweep.  Float-float: value add, fence, children count, fence.
 template <class V>
 __global__ void k_top_walk(const uint32_t* par, V* fin, uint32_t* deg, const uint32_t* list, uint32_t* counters) {
   const uint32_t n = *(volatile const uint32_t*)&counters[0];
   uint32_t done = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t x = list[i];
-    V v = fin[x];
-    done++;
-    for (;;) {
-      const uint32_t p = par[x];
-      if (p == ROOT) break;
-      vatomic_add(&fin[p], v);
-      __threadfence();
-      if (atomicSub(&deg[p], 1u) != 1u) break;
-      __threadfence();
-      x = p;
-      v = vload_volatile(&fin[p]);
+  if constexpr (std::is_same<V, uint32_t>::value) {
+    unsigned long long* fd = reinterpret_cast<unsigned long long*>(deg);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      uint32_t x = list[i];
+      uint32_t v = (uint32_t)fd[x];  // a source: its own value
+      for (;;) {
+        fin[x] = v;
+        done++;
+        const uint32_t p = par[x];
+        if (p == ROOT) break;
+        const unsigned long long old = atomicAdd(&fd[p], (unsigned long long)v - (1ull << 32));
+        if ((old >> 32) != 1ull) break;
+        v += (uint32_t)old;
+        x = p;
+      }
+    }
+  } else {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      uint32_t x = list[i];
+      V v = fin[x];
       done++;
+      for (;;) {
+        const uint32_t p = par[x];
+        if (p == ROOT) break;
+        vatomic_add(&fin[p], v);
+        __threadfence();
+        if (atomicSub(&deg[p], 1u) != 1u) break;
+        __threadfence();
+        x = p;
+        v = vload_volatile(&fin[p]);
+        done++;
+      }
     }
   }
   if (done) atomicAdd(&counters[2], done);
@@ -488,7 +522,7 @@ static cudaError_t launch_level_down(const DemTable& cdt, const DemTable& gdt, c
 template <int S, class V, class CV>
 static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& top, cudaStream_t s, int* nl) {
   const int64_t ns = lv.nunits * 4 * S;
-  cudaError_t e = cudaMemsetAsync(top.deg, 0, sizeof(uint32_t) * (size_t)ns, s);
+  cudaError_t e = cudaMemsetAsync(top.deg, 0, sizeof(unsigned long long) * (size_t)ns, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(top.counters, 0, sizeof(uint32_t) * 4, s);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 1;
@@ -499,7 +533,8 @@ static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& 
   if (b < 1) b = 1;
   k_top_init<S, V, CV><<<(unsigned)b, 256, 0, s>>>(dt, lv.pex, static_cast<const CV*>(lv.pval),
                                                    static_cast<V*>(lv.fin), top.par, top.deg, ns);
-  k_top_sources<<<(unsigned)b, 256, 0, s>>>(lv.pex, top.deg, top.list, top.counters, ns);
+  k_top_sources<std::is_same<V, uint32_t>::value><<<(unsigned)b, 256, 0, s>>>(lv.pex, top.deg, top.list,
+                                                                             top.counters, ns);
   k_top_walk<V><<<(unsigned)(sms * 8), 256, 0, s>>>(top.par, static_cast<V*>(lv.fin), top.deg, top.list,
                                                     top.counters);
   k_top_check<<<1, 32, 0, s>>>(top.counters, top.status);
