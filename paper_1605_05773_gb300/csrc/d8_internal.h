@@ -48,9 +48,9 @@ struct Pipe {
   int rounds;
   uint16_t* pex;     // per slot: exit code of the in-tile path
   void* pval;        // per slot: in-tile area at exits (fwd) / path sum (bwd)
-  uint32_t* P[2];    // combine: pointer-jumping parents (ping-pong)
-  void* S;           // combine: values (fwd: in place; bwd: ping-pong with S2)
-  void* S2;          // combine: second value buffer (bwd) / delta buffer (fwd)
+  uint32_t* P[2];    // flat combines (adjoint, allocation-free entry): pointer-jumping parents
+  void* S;           // per slot: final value at exits, read by the finalising pass
+  void* S2;          // flat combines: second value buffer (adjoint) / delta buffer (counts)
   uint32_t* flags;   // combine: per-round "still active" flags, MAX_ROUNDS+2
   uint32_t* status;  // device status word (OR of 1 << d8_status)
   uint32_t* queue;   // tile work-queue counters (one per stage)
@@ -88,7 +88,7 @@ struct HLevel {
 };
 struct HTop {  // the top level's queue-method solve in global memory
   uint32_t* par;
-  uint32_t* deg;
+  uint32_t* deg;  // 8 bytes per slot: unit counts pack children left (high) and value (low)
   uint32_t* list;
   uint32_t* counters;  // [0] sources, [1] exits, [2] finished
   uint32_t* status;
@@ -106,7 +106,7 @@ struct HPlan {
 int hier_levels(int T, int64_t max_side, int* S, int* G, int max_levels);
 cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch);
 
-// unit-count tile passes (d8_unit.cu)
+// tile passes, unit counts or weighted (d8_unit.cu)
 cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s);
 cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s);
 
