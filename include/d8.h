@@ -68,6 +68,20 @@ d8_status d8_destroy(d8_ctx* ctx);
  * memory.  D8_ERR_ARG for any other value. */
 d8_status d8_set_tile(d8_ctx* ctx, int tile);
 
+/* Frontier strategy used by later calls (and by batch plans made later): how
+ * the chains of the flow forest are traversed.  0 = chain walks ("last input
+ * continues", Algorithm 2's tail recursion) fed from a per-warp ring of
+ * pending sources refilled by warp votes in the tiles, and the queue method
+ * (Algorithm 6) with one walk per chain at the combine's top level
+ * (default); 1 = the tiles' walks fed from per-thread source bit masks, idle
+ * lanes served by lanes with sources to spare; 2 = ring walks in the tiles
+ * and pointer jumping at the top level (every exit adds its partial sum to
+ * its 2^r-th ancestor, then jumps, for ceil(log2(depth)) rounds), for DEMs
+ * whose channels cross tile borders very many times.  Unit counts are
+ * identical under every strategy; weighted sums may differ in the last bits
+ * (their order of addition changes).  D8_ERR_ARG for any other value. */
+d8_status d8_set_strategy(d8_ctx* ctx, int strategy);
+
 /* D8 flow direction of every cell ("The Algorithm"; "Introduction").
  * z: H x W fp32 elevations (ld ldz); dir: H x W codes (ld lddir).
  * Non-finite z sets D8_ERR_NONFINITE in the status word and gives that cell
@@ -87,9 +101,11 @@ d8_status d8_flowdir(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t 
 d8_status d8_accumulate(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir, uint32_t* A,
                         int64_t ldA, d8_stream stream);
 
-/* Directions and unit counts in one pipeline: the direction stencil is fused
- * into the first per-tile pass, so z is read once and dir written once.
- * Same arguments and errors as d8_flowdir + d8_accumulate. */
+/* Directions and unit counts in one call: the direction stencil writes dir,
+ * then the per-tile passes, the combine and the finalising pass of
+ * d8_accumulate run on it (z is read once; dir is written once and read back
+ * by the tile passes).  Same arguments and errors as d8_flowdir +
+ * d8_accumulate. */
 d8_status d8_flowdir_accumulate(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
                                 uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA, d8_stream stream);
 
@@ -183,12 +199,17 @@ const char* d8_version(void);
  * z, dir, A: as d8_flowdir_accumulate (device pointers on the current device,
  * owned by the caller).  status: optional device pointer to one uint32 that
  * the call first clears and then ORs device-side errors into as
- * (1 << d8_status) bits (non-finite z, invalid code, cycle); NULL discards
- * them.  Asynchronous on `stream`.
+ * (1 << d8_status) bits (non-finite z, invalid code, cycle); with NULL the
+ * errors go to a status word inside the shared scratch instead, which every
+ * call clears and writes, so they cannot be read back reliably.
+ * Asynchronous on `stream`.
  *
  * The first call on a device looks up the device address of the scratch
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before capturing any stream into a CUDA graph.  All calls share the one
+ * before capturing any stream into a CUDA graph.  The address is kept for
+ * the life of the process: after cudaDeviceReset on a device it is stale, so
+ * do not call this entry point on that device again in the same process.
+ * All calls share the one
  * scratch array and it keeps the previous call's contents (the call clears
  * what must start at zero itself); calls whose GPU work can overlap in time --
  * on different streams or from different threads without ordering between

@@ -21,13 +21,15 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "load", "flowdir", "accumulate", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
+    "load", "flowdir", "accumulate", "set_strategy", "STRATEGIES", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
     "weighted_upslope", "WeightedUpslope", "BatchPlan", "autotune_batch", "get_status", "set_tile", "set_profiling",
     "stage_times", "D8Error", "OUTLET", "SINK", "RULES",
 ]
 
 OUTLET, SINK = 8, 9
 RULES = {"steepest": 0, "lowest": 1}
+# in-tile frontier strategies of the unit-count tile passes (identical results)
+STRATEGIES = {"ring": 0, "lane_mask": 1, "jump": 2}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_NONFINITE", 4: "ERR_CYCLE", 5: "ERR_NOMEM",
           6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
 
@@ -35,6 +37,7 @@ _lib = None
 _lock = threading.Lock()
 _ctx: dict[int, ctypes.c_void_p] = {}
 _tile: int = 64
+_strategy: int = 0
 _profiling: bool = False
 
 
@@ -69,6 +72,7 @@ def load() -> ctypes.CDLL:
             "d8_create": [ctypes.POINTER(vp), i32],
             "d8_destroy": [vp],
             "d8_set_tile": [vp, i32],
+            "d8_set_strategy": [vp, i32],
             "d8_flowdir": [vp, vp, i64, i64, i64, vp, i64, i32, vp],
             "d8_accumulate": [vp, vp, i64, i64, i64, vp, i64, vp],
             "d8_flowdir_accumulate": [vp, vp, i64, i64, i64, i32, vp, i64, vp, i64, vp],
@@ -112,6 +116,7 @@ def context(device=None) -> ctypes.c_void_p:
         h = ctypes.c_void_p()
         _check(L.d8_create(ctypes.byref(h), idx), "d8_create")
         _check(L.d8_set_tile(h, _tile), "d8_set_tile")
+        _check(L.d8_set_strategy(h, _strategy), "d8_set_strategy")
         L.d8_set_profiling(h, 1 if _profiling else 0)
         _ctx[idx] = h
     return _ctx[idx]
@@ -122,6 +127,18 @@ def set_tile(tile: int, device=None):
     global _tile
     _tile = int(tile)
     _check(load().d8_set_tile(context(device), _tile), "d8_set_tile")
+
+
+def set_strategy(strategy, device=None):
+    """Frontier strategy for later calls: "ring" (0, the default: chain walks
+    fed from a per-warp ring in the tiles, queue walk at the combine's top
+    level), "lane_mask" (1: the tiles' walks fed from per-thread source
+    masks) or "jump" (2: ring walks in the tiles, pointer jumping at the top
+    level, for DEMs whose channels cross tile borders very many times).
+    Counts are identical; weighted sums may differ in the last bits."""
+    global _strategy
+    _strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+    _check(load().d8_set_strategy(context(device), _strategy), "d8_set_strategy")
 
 
 def set_profiling(on: bool, device=None):

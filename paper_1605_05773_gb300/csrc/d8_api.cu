@@ -39,6 +39,7 @@ int bit_width(uint64_t x) {
 struct d8_ctx {
   int device = 0;
   int T = 64;
+  int strat = d8::STRAT_RING;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   uint32_t* status = nullptr;
@@ -53,6 +54,7 @@ struct d8_batch {
   d8_ctx* ctx = nullptr;
   int n = 0;
   int T = 64;
+  int strat = d8::STRAT_RING;
   std::vector<DemDesc> host_desc;
   DemDesc* dev_desc = nullptr;
   int32_t* dev_tile_dem = nullptr;
@@ -192,7 +194,8 @@ size_t hier_bytes(const HShape& hs, size_t vb) {
     b += align256(ns * 2) + 2 * align256(ns * vb);
   }
   const size_t nt = (size_t)hs.nunits[hs.nlev] * 4 * hs.S[hs.nlev];
-  if (hs.need_top) b += 2 * align256(nt * 4) + align256(nt * 8);  // par, list; children counts (8 B: packed)
+  // par, par2, list; children counts or additions (8 B); round flags
+  if (hs.need_top) b += 3 * align256(nt * 4) + align256(nt * 8) + align256(sizeof(uint32_t) * (MAX_ROUNDS + 2));
   b += align256(sizeof(uint32_t) * 64);
   return b;
 }
@@ -202,6 +205,7 @@ size_t hier_bytes(const HShape& hs, size_t vb) {
 HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dts, bool weighted) {
   HPlan hp{};
   hp.weighted = weighted;
+  hp.top.jump = p.strat == STRAT_JUMP;
   hp.nlev = hs.nlev;
   hp.need_top = hs.need_top;
   hp.status = p.status;
@@ -230,10 +234,14 @@ HPlan carve_hier(void* base, const HShape& hs, const Pipe& p, const DemTable* dt
   if (hs.need_top) {
     hp.top.par = reinterpret_cast<uint32_t*>(q);
     q += align256(nt * 4);
+    hp.top.par2 = reinterpret_cast<uint32_t*>(q);
+    q += align256(nt * 4);
     hp.top.deg = reinterpret_cast<uint32_t*>(q);  // 8 bytes per slot (unit counts pack value and count)
     q += align256(nt * 8);
     hp.top.list = reinterpret_cast<uint32_t*>(q);
     q += align256(nt * 4);
+    hp.top.flags = reinterpret_cast<uint32_t*>(q);
+    q += align256(sizeof(uint32_t) * (MAX_ROUNDS + 2));
   }
   hp.queue = reinterpret_cast<uint32_t*>(q);
   hp.top.counters = hp.queue + 48;
@@ -294,6 +302,7 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   d8_status st = ensure_ws(c, pb + hb);
   if (st != D8_OK) return st;
   Pipe p = carve_pipe(c->ws, ntiles, T, vb, c->status);
+  p.strat = c->strat;
   DemTable dt = single(d);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -391,6 +400,12 @@ d8_status d8_destroy(d8_ctx* c) {
 d8_status d8_set_tile(d8_ctx* c, int tile) {
   if (!c || (tile != 32 && tile != 64 && tile != 128)) return D8_ERR_ARG;
   c->T = tile;
+  return D8_OK;
+}
+
+d8_status d8_set_strategy(d8_ctx* c, int strategy) {
+  if (!c || strategy < 0 || strategy >= STRAT_COUNT) return D8_ERR_ARG;
+  c->strat = strategy;
   return D8_OK;
 }
 
@@ -554,6 +569,7 @@ d8_status d8_batch_plan(d8_ctx* c, int n, const int64_t* H, const int64_t* W, d8
   b->ctx = c;
   b->n = n;
   b->T = c->T;
+  b->strat = c->strat;
   b->host_desc.resize(n);
   int64_t base = 0;
   for (int k = 0; k < n; k++) {
@@ -635,6 +651,7 @@ static cudaError_t batch_enqueue(d8_batch* b, int rule, cudaStream_t s, int* n_u
   dt.one = b->host_desc[0];
   if (b->n == 1) dt.ndem = 1;
   Pipe p = carve_pipe(b->ws, b->ntiles, b->T, 4, b->ctx->status);
+  p.strat = b->strat;
   HShape hs;
   hs.nlev = b->nlev;
   hs.need_top = b->need_top;

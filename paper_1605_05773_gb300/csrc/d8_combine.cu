@@ -478,6 +478,113 @@ __global__ void k_top_check(const uint32_t* counters, uint32_t* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && counters[1] != counters[2]) set_status(status, D8_ERR_CYCLE);
 }
 
+// ---- top level by pointer jumping (strategy 2).  The queue walk above costs
+// one dependent global atomic per node of the longest chain, which a channel
+// crossing the top-level units 10^5 times makes tens of milliseconds.  Here
+// every exit y keeps P(y) = its 2^r-th ancestor (ROOT past the root); a round
+// adds each exit's partial sum to P(y) and jumps (P(y) = P(P(y))), the sums
+// are applied, and after ceil(log2(depth)) rounds every exit holds its
+// subtree sum (Algorithm 6's result) in fin.  Rounds after the last active
+// one return at once (a per-round flag).
+
+// parents, values (fin = pval at exits), additions zeroed, first round flag
+template <int S, class V, class CV>
+__global__ void k_topj_init(DemTable dt, const uint16_t* pex, const CV* pval, V* fin, uint32_t* par, V* add,
+                            uint32_t* flags, int64_t nslots) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool any = false;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nslots; g += stride) {
+    const uint16_t pe = pex[g];
+    uint32_t pr = ROOT;
+    if (pe & PEX_EXIT) {
+      const int64_t t = g / (4 * S);
+      const int s = (int)(g - t * (4 * S));
+      const DemDesc d = dem_of(dt, t);
+      const int64_t lt = t - d.tile_base;
+      const UnitGeo u = unit_geo(d, lt / d.ntx, lt % d.ntx, S);
+      int i, j;
+      slot_cell(s, u.h, u.w, S, i, j);
+      const int k = pe & 7;
+      const int64_t y = global_slot(d, u.i0 + i + code_di(k), u.j0 + j + code_dj(k), S);
+      const uint16_t pey = pex[y];
+      if (pey & PEX_EXIT)
+        pr = (uint32_t)y;
+      else if (pey != PEX_TERM)
+        pr = (uint32_t)((y / (4 * S)) * (4 * S) + pey);
+      fin[g] = V(pval[g]);
+      add[g] = V{};
+      any |= pr != ROOT;
+    }
+    par[g] = pr;
+  }
+  if (__syncthreads_or(any) && threadIdx.x == 0) flags[0] = 1u;
+}
+
+// one round over the listed exits: scatter to the 2^r-th ancestor, then jump
+template <class V>
+__global__ void k_topj_round(const uint32_t* list, const uint32_t* counters, const uint32_t* pc, uint32_t* pn,
+                             const V* fin, V* add, uint32_t* flags, int r) {
+  if (*(volatile const uint32_t*)&flags[r] == 0u) return;
+  const uint32_t n = counters[0];
+  bool active = false;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t y = list[i];
+    const uint32_t a = pc[y];
+    if (a == ROOT) {
+      pn[y] = ROOT;
+      continue;
+    }
+    vatomic_add(&add[a], fin[y]);
+    const uint32_t aa = pc[a];
+    pn[y] = aa;
+    active |= aa != ROOT;
+  }
+  if (__syncthreads_or(active) && threadIdx.x == 0) flags[r + 1] = 1u;
+}
+
+template <class V>
+__global__ void k_topj_apply(const uint32_t* list, const uint32_t* counters, V* fin, V* add, const uint32_t* flags,
+                             int r) {
+  if (*(volatile const uint32_t*)&flags[r] == 0u) return;
+  const uint32_t n = counters[0];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t y = list[i];
+    const V dv = add[y];
+    fin[y] = vadd(fin[y], dv);
+    add[y] = V{};
+  }
+}
+
+// exits still jumping after the last round: the exit forest has a cycle
+__global__ void k_topj_check(const uint32_t* flags, int R, uint32_t* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && flags[R] != 0u) set_status(status, D8_ERR_CYCLE);
+}
+
+// every exit listed (same scheme as k_top_sources: one atomic per block)
+__global__ void __launch_bounds__(256) k_topj_list(const uint16_t* pex, uint32_t* list, uint32_t* counters,
+                                                   int64_t nslots) {
+  __shared__ uint32_t sh[256];
+  __shared__ uint32_t sh_base;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t nex = 0;
+  for (int64_t g = g0; g < nslots; g += stride) nex += (pex[g] & PEX_EXIT) != 0;
+  sh[threadIdx.x] = nex;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const uint32_t a = threadIdx.x >= off ? sh[threadIdx.x - off] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += a;
+    __syncthreads();
+  }
+  if (threadIdx.x == 255) sh_base = sh[255] ? atomicAdd(&counters[0], sh[255]) : 0u;
+  __syncthreads();
+  uint32_t pos = sh_base + sh[threadIdx.x] - nex;
+  if (nex)
+    for (int64_t g = g0; g < nslots; g += stride)
+      if (pex[g] & PEX_EXIT) list[pos++] = (uint32_t)g;
+}
+
 template <int S, int G, class V, class CV>
 static cudaError_t launch_level_up(const DemTable& cdt, const DemTable& gdt, const uint16_t* cpex, const void* cpval,
                                    uint16_t* gpex, void* gpval, int64_t ngroups, uint32_t* queue, uint32_t* status,
@@ -520,7 +627,39 @@ static cudaError_t launch_level_down(const DemTable& cdt, const DemTable& gdt, c
 }
 
 template <int S, class V, class CV>
+static cudaError_t launch_top_jump(const DemTable& dt, const HLevel& lv, const HTop& top, cudaStream_t s, int* nl) {
+  const int64_t ns = lv.nunits * 4 * S;
+  cudaError_t e = cudaMemsetAsync(top.flags, 0, sizeof(uint32_t) * (MAX_ROUNDS + 2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(top.counters, 0, sizeof(uint32_t) * 4, s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (ns + 255) / 256;
+  if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
+  if (b < 1) b = 1;
+  V* fin = static_cast<V*>(lv.fin);
+  V* add = reinterpret_cast<V*>(top.deg);
+  k_topj_init<S, V, CV><<<(unsigned)b, 256, 0, s>>>(dt, lv.pex, static_cast<const CV*>(lv.pval), fin, top.par, add,
+                                                    top.flags, ns);
+  k_topj_list<<<(unsigned)b, 256, 0, s>>>(lv.pex, top.list, top.counters, ns);
+  // rounds: enough for a chain through every slot
+  int R = 1;
+  while (R < MAX_ROUNDS && ((int64_t)1 << R) < ns) R++;
+  for (int r = 0; r < R; r++) {
+    uint32_t* pc = (r & 1) ? top.par2 : top.par;
+    uint32_t* pn = (r & 1) ? top.par : top.par2;
+    k_topj_round<V><<<(unsigned)b, 256, 0, s>>>(top.list, top.counters, pc, pn, fin, add, top.flags, r);
+    k_topj_apply<V><<<(unsigned)b, 256, 0, s>>>(top.list, top.counters, fin, add, top.flags, r);
+  }
+  k_topj_check<<<1, 32, 0, s>>>(top.flags, R, top.status);
+  *nl += 3 + 2 * R;
+  return cudaGetLastError();
+}
+
+template <int S, class V, class CV>
 static cudaError_t launch_top(const DemTable& dt, const HLevel& lv, const HTop& top, cudaStream_t s, int* nl) {
+  if (top.jump) return launch_top_jump<S, V, CV>(dt, lv, top, s, nl);
   const int64_t ns = lv.nunits * 4 * S;
   cudaError_t e = cudaMemsetAsync(top.deg, 0, sizeof(unsigned long long) * (size_t)ns, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(top.counters, 0, sizeof(uint32_t) * 4, s);

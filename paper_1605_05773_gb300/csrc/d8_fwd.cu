@@ -9,6 +9,7 @@
 //             reaches next) and its subtree sums are found by pointer jumping
 //             with scatter-adds, ceil(log2(depth)) rounds.  The context entry
 //             points use the layered combine (d8_combine.cu).
+#include <atomic>
 #include <cstdio>
 
 #include "d8_device.cuh"
@@ -94,15 +95,22 @@ __global__ void k_pj_check(Pipe p, int R) {
 // ---------------------------------------------------------------------------
 // host launchers
 
-static int g_num_sms = 0;
+// SM count of the current device, cached per device index (the calls may
+// come from several host threads and several devices)
+static std::atomic<int> g_num_sms[64];
 static int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  int n = g_num_sms[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 1;
+    }
+    g_num_sms[dev].store(n, std::memory_order_relaxed);
   }
-  return g_num_sms;
+  return n;
 }
 
 static unsigned grid_for(int64_t n, int per_thread_block = 256) {

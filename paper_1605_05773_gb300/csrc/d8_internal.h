@@ -42,8 +42,16 @@ enum UpMode { UP_UNIT_DIR = 0, UP_UNIT_Z = 1, UP_WEIGHTED = 2 };
 
 // Device workspace of one pipeline run (all arrays indexed by global slot id
 // = tile * 4T + slot unless noted).
+// In-tile frontier strategies of the unit-count tile pass (the weighted pass
+// always uses the ring): how a lane whose walk stopped finds its next source.
+// Strategy 2 keeps the ring walks in the tiles and replaces the combine's
+// top-level queue walk by pointer jumping, for DEMs whose exit forest holds
+// very long chains (a channel that crosses tile borders many times).
+enum Strategy { STRAT_RING = 0, STRAT_LANE_MASK = 1, STRAT_JUMP = 2, STRAT_COUNT = 3 };
+
 struct Pipe {
   int T;
+  int strat;  // Strategy of the unit-count tile pass
   int64_t ntiles, nslots;
   int rounds;
   uint16_t* pex;     // per slot: exit code of the in-tile path
@@ -86,9 +94,13 @@ struct HLevel {
   void* pval;       // uint32 / ff
   void* fin;        // uint32 / ff
 };
-struct HTop {  // the top level's queue-method solve in global memory
+struct HTop {  // the top level's solve in global memory (queue method or pointer jumping)
+  bool jump;      // pointer jumping instead of the queue walk
   uint32_t* par;
-  uint32_t* deg;  // 8 bytes per slot: unit counts pack children left (high) and value (low)
+  uint32_t* par2;  // pointer jumping: the second parent buffer
+  uint32_t* flags; // pointer jumping: per-round "still active" flags (MAX_ROUNDS + 2)
+  uint32_t* deg;  // 8 bytes per slot: unit counts pack children left (high) and value (low);
+                  // pointer jumping: this round's additions (value type)
   uint32_t* list;
   uint32_t* counters;  // [0] sources, [1] exits, [2] finished
   uint32_t* status;

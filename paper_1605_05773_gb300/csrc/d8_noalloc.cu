@@ -106,6 +106,7 @@ extern "C" d8_status d8_flowdir_accumulate_noalloc(const float* z, int64_t H, in
   // carve the pipeline arrays out of the scratch
   d8::Pipe p{};
   p.T = NA_TILE;
+  p.strat = d8::STRAT_RING;
   p.ntiles = ntiles;
   p.nslots = ntiles * 4 * NA_TILE;
   p.rounds = bits((uint64_t)p.nslots);

@@ -275,6 +275,57 @@ __device__ __forceinline__ ff pull_value(const ff* val, int c, uint32_t w) {
   return v;
 }
 
+// Perimeter summary of a finished tile: for each perimeter slot, the exit of
+// the cell's in-tile path (Algorithms 3-4 seen from the exit side) found by a
+// chase over the walks' segment records (resolved records are written back),
+// and the in-tile count / area at the slot.
+template <int T, bool WT>
+__device__ __forceinline__ void perimeter_summary(const TileGeo& g, int64_t t, const uint32_t* word, uint16_t* seg,
+                                                  const ff* val, bool cyc, const Pipe& p) {
+  using W = WL<T>;
+  constexpr int TT = T * T;
+  constexpr int NT = UpThreads<T, WT>::N;
+  for (int s = threadIdx.x; s < 4 * T; s += NT) {
+    int i, j;
+    uint16_t pe = PEX_TERM;
+    uint32_t pv = 0;
+    ff pvw{0.0f, 0.0f};
+    if (slot_cell(s, g.th, g.tw, T, i, j)) {
+      const int c = i * T + j;
+      const uint32_t w = word[c];
+      if (WT)
+        pvw = val[c];
+      else
+        pv = W::cnt(w);
+      if (w & W_EXIT) {
+        pe = (uint16_t)(PEX_EXIT | W::code(w));
+      } else if ((w & W_IN) && !cyc) {
+        volatile uint16_t* vs = seg;
+        const uint16_t v = vs[c];
+        const int hh = (v & SEG_REC) ? c : (int)(v & (TT - 1));
+        uint16_t r = (v & SEG_REC) ? v : vs[hh];
+        for (int guard = 0; !(r & SEG_END) && guard < TT; guard++) {
+          const int jn = r & (TT - 1);  // junction: continue with the walk that finished it
+          const uint16_t vj = vs[jn];
+          r = (vj & SEG_REC) ? vj : vs[vj & (TT - 1)];
+        }
+        if (r & SEG_END) {
+          vs[hh] = r;  // path compression
+          const int e = r & (TT - 1);
+          if (word[e] & W_EXIT) pe = (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T);
+        } else {
+          set_status(p.status, D8_ERR_CYCLE);
+        }
+      }
+    }
+    p.pex[t * (4 * T) + s] = pe;
+    if (WT)
+      static_cast<ff*>(p.pval)[t * (4 * T) + s] = pvw;
+    else
+      static_cast<uint32_t*>(p.pval)[t * (4 * T) + s] = pv;
+  }
+}
+
 template <int T, bool WT>
 __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p) {
   constexpr int NT = UpThreads<T, WT>::N;
@@ -382,47 +433,141 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(Dem
       store_areas<T>(d, g, val);
     else
       store_counts<T>(d, g, word);
-    // perimeter summary: the exit of each perimeter cell's in-tile path, by a
-    // chase over segment records (resolved records are written back)
-    for (int s = threadIdx.x; s < 4 * T; s += NT) {
-      int i, j;
-      uint16_t pe = PEX_TERM;
-      uint32_t pv = 0;
-      ff pvw{0.0f, 0.0f};
-      if (slot_cell(s, g.th, g.tw, T, i, j)) {
-        const int c = i * T + j;
-        const uint32_t w = word[c];
-        if (WT)
-          pvw = val[c];
-        else
-          pv = W::cnt(w);
-        if (w & W_EXIT) {
-          pe = (uint16_t)(PEX_EXIT | W::code(w));
-        } else if ((w & W_IN) && !cyc) {
-          volatile uint16_t* vs = seg;
-          const uint16_t v = vs[c];
-          const int hh = (v & SEG_REC) ? c : (int)(v & (TT - 1));
-          uint16_t r = (v & SEG_REC) ? v : vs[hh];
-          for (int guard = 0; !(r & SEG_END) && guard < TT; guard++) {
-            const int jn = r & (TT - 1);  // junction: continue with the walk that finished it
-            const uint16_t vj = vs[jn];
-            r = (vj & SEG_REC) ? vj : vs[vj & (TT - 1)];
+    perimeter_summary<T, WT>(g, t, word, seg, val, cyc, p);
+  }
+}
+
+// The unit-count tile pass with the lane-mask walk (frontier strategy 1).
+// Same codes phase, walks, segment records and perimeter summary as
+// k_up_unit; only the way idle lanes find sources differs.  Thread t owns
+// the cells t + NTU * r (r = 0 .. T*T/NTU - 1) and, once the in-tile input
+// counts are complete, holds which of them are sources as a bit mask in
+// registers.  A lane whose walk stopped takes its own next source (find-first-
+// set, no warp vote); only when a lane has none left does the warp pair its
+// idle lanes with lanes that still have spare sources, each donor handing over
+// its last one through a 32-entry per-warp mailbox in shared memory.  The loop
+// body is a handful of instructions when no lane is out of work, against a
+// ballot-driven ring refill on every step in k_up_unit.
+template <int T>
+struct LaneMask {
+  static constexpr int CPT = T * T / NTU;     // cells per thread
+  static constexpr int NM = (CPT + 31) / 32;  // 32-bit mask words per thread
+};
+
+template <int T>
+__global__ void __launch_bounds__(NTU, 8) k_up_lm(DemTable dt, Pipe p) {
+  using L = UpLayout<T, false>;
+  using W = WL<T>;
+  constexpr int TT = T * T;
+  constexpr int CPT = LaneMask<T>::CPT, NM = LaneMask<T>::NM;
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint32_t* word = reinterpret_cast<uint32_t*>(sm + L::off_word);
+  uint16_t* seg = reinterpret_cast<uint16_t*>(sm + L::off_seg);
+  uint16_t* offer = reinterpret_cast<uint16_t*>(sm + L::off_ring) + (threadIdx.x >> 5) * 32;
+  int* misc = reinterpret_cast<int*>(sm + L::off_misc);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+
+  TileQueue tq(p.queue + 0, p.ntiles);
+  for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
+    const DemDesc d = dem_of(dt, t);
+    const TileGeo g = tile_geo(d, t - d.tile_base, T);
+    uint4* w4 = reinterpret_cast<uint4*>(word);
+    for (int c = threadIdx.x; c < TT / 4; c += NTU) w4[c] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) misc[0] = 0;
+    __syncthreads();
+    tile_codes_from_dir<T, false>(d, g, word, nullptr, p.status);  // Algorithm 1
+    __syncthreads();
+    // this thread's sources: count 1 and no input left (absent cells of a
+    // ragged tile have count 0)
+    uint32_t m[NM];
+#pragma unroll
+    for (int k = 0; k < NM; k++) m[k] = 0u;
+#pragma unroll
+    for (int r = 0; r < CPT; r++)
+      m[r / 32] |= (uint32_t)((word[threadIdx.x + NTU * r] & W::SRC_MASK) == 1u) << (r % 32);
+    // Algorithm 2: walk down-slope while last to arrive
+    int done = 0;
+    {
+      int cur = -1, h = 0;
+      uint32_t acc = 0, wv = 0;
+      for (;;) {
+        if (cur < 0) {
+#pragma unroll
+          for (int k = 0; k < NM; k++) {
+            if (m[k]) {
+              const int r = __ffs(m[k]) - 1;
+              m[k] &= m[k] - 1u;
+              cur = threadIdx.x + NTU * (32 * k + r);
+              break;
+            }
           }
-          if (r & SEG_END) {
-            vs[hh] = r;  // path compression
-            const int e = r & (TT - 1);
-            if (word[e] & W_EXIT) pe = (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T);
+          if (cur >= 0) {
+            h = cur;
+            wv = word[cur];
+            acc = 1;
+            done++;
+          }
+        }
+        const unsigned idle = __ballot_sync(FULL, cur < 0);
+        if (idle) {
+          bool spare = false;
+#pragma unroll
+          for (int k = 0; k < NM; k++) spare |= (m[k] != 0u);
+          const unsigned donors = __ballot_sync(FULL, spare);
+          if (!donors) {
+            if (idle == FULL) break;
           } else {
-            set_status(p.status, D8_ERR_CYCLE);
+            const int ni = __popc(idle), nd = __popc(donors);
+            if (spare && __popc(donors & lt) < ni) {  // hand over the last own source
+#pragma unroll
+              for (int k = NM - 1; k >= 0; k--) {
+                if (m[k]) {
+                  const int r = 31 - __clz(m[k]);
+                  m[k] &= ~(1u << r);
+                  offer[__popc(donors & lt)] = (uint16_t)(threadIdx.x + NTU * (32 * k + r));
+                  break;
+                }
+              }
+            }
+            __syncwarp();
+            if (cur < 0 && __popc(idle & lt) < nd) {
+              cur = offer[__popc(idle & lt)];
+              h = cur;
+              wv = word[cur];
+              acc = 1;
+              done++;
+            }
+            __syncwarp();  // the mailbox is read before it is written again
+          }
+        }
+        if (cur >= 0) {
+          if (wv & W_IN) {
+            const int s = W::next(wv, cur);
+            const uint32_t old = atomicAdd(&word[s], acc - W_LEFT1);
+            if (W::last(old)) {  // last input to arrive: continue there
+              seg[s] = (uint16_t)h;
+              acc += W::cnt(old);
+              wv = old;
+              cur = s;
+              done++;
+            } else {
+              seg[h] = (uint16_t)(SEG_REC | s);
+              cur = -1;
+            }
+          } else {
+            seg[h] = (uint16_t)(SEG_REC | SEG_END | cur);
+            cur = -1;
           }
         }
       }
-      p.pex[t * (4 * T) + s] = pe;
-      if (WT)
-        static_cast<ff*>(p.pval)[t * (4 * T) + s] = pvw;
-      else
-        static_cast<uint32_t*>(p.pval)[t * (4 * T) + s] = pv;
     }
+    atomicAdd(&misc[0], done);
+    __syncthreads();
+    const bool cyc = misc[0] != g.th * g.tw;
+    if (threadIdx.x == 0 && cyc) set_status(p.status, D8_ERR_CYCLE);
+    store_counts<T>(d, g, word);
+    perimeter_summary<T, false>(g, t, word, seg, nullptr, cyc, p);
   }
 }
 
@@ -719,7 +864,7 @@ static unsigned persistent_grid_u(K kernel, int threads, size_t smem, int64_t nt
 template <int T, bool WT>
 static cudaError_t launch_up_unit_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
   const size_t bytes = UpLayout<T, WT>::bytes;
-  auto k = k_up_unit<T, WT>;
+  auto k = (!WT && p.strat == STRAT_LANE_MASK) ? k_up_lm<T> : k_up_unit<T, WT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k<<<persistent_grid_u(k, UpThreads<T, WT>::N, bytes, p.ntiles), UpThreads<T, WT>::N, bytes, s>>>(dt, p);

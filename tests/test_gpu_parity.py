@@ -9,7 +9,7 @@ import torch
 
 import demgen
 import oracle
-from tests import brute
+from tests import brute, oracle_cache
 from tests.gpu_util import recursion_residual_gpu, spiral_dirs, terminal_sum_gpu, to_dev, u32
 
 pytestmark = pytest.mark.gpu
@@ -116,6 +116,43 @@ def test_figure1_paths_small_tiles(d8):
         d8.set_tile(64)
 
 
+@pytest.mark.parametrize("strategy", ["ring", "lane_mask", "jump"])
+def test_strategies_bit_exact(d8, strategy):
+    """Every frontier strategy gives the oracle's counts: fractal DEMs under
+    both rules (ragged shapes, and one large enough for a top level above the
+    512-cell groups), serpentine and spiral fields (one chain through many
+    tiles), and random acyclic fields with terminals, at every tile side."""
+    d8.set_strategy(strategy)
+    try:
+        for T in TILES:
+            d8.set_tile(T)
+            for H, W, seed in ((512, 512, 1605), (333, 517, 7), (130, 65, 8)):
+                z = demgen.fractal(H, W, seed=seed, cache=False)
+                for rule in RULES:
+                    d, A = _fused(d8, z, rule)
+                    d_ref = oracle.flowdir(z, rule)
+                    np.testing.assert_array_equal(d, d_ref)
+                    np.testing.assert_array_equal(A, oracle.accumulate(d_ref))
+            z = demgen.fractal(1500, 1100, seed=9, cache=False)  # big enough for a top level above 512
+            d, A = _fused(d8, z, "steepest")
+            d_ref = oracle.flowdir(z)
+            np.testing.assert_array_equal(d, d_ref)
+            np.testing.assert_array_equal(A, oracle.accumulate(d_ref))
+            rng = np.random.default_rng(T)
+            fields = [demgen.serpentine_dirs(200, 190), spiral_dirs(150, 170),
+                      rng.choice(np.array([2, 3, 4, 5, 8, 9], dtype=np.uint8), size=(257, 129),
+                                 p=[.2, .2, .3, .2, .05, .05]),
+                      demgen.serpentine_dirs(1300, 1100), spiral_dirs(1200, 1000)]
+            for f in fields:
+                A = d8.accumulate(to_dev(f))
+                torch.cuda.synchronize()
+                assert d8.get_status() == "OK"
+                np.testing.assert_array_equal(u32(A), oracle.accumulate(f))
+    finally:
+        d8.set_tile(64)
+        d8.set_strategy("ring")
+
+
 def test_tile_size_invariance(d8):
     z = demgen.fractal(700, 555, seed=77, cache=False)
     outs = []
@@ -173,39 +210,69 @@ def dem8192():
     return demgen.fractal(8192, 8192)
 
 
+@pytest.mark.parametrize("rule", RULES)
 @pytest.mark.parametrize("kind", ["fractal", "plane", "serpentine_dem"])
-def test_8192_fused_full_oracle(d8, kind, dem8192):
+def test_8192_fused_full_oracle(d8, kind, rule, dem8192):
+    """The three 8192^2 structures under both direction rules: directions and
+    counts against the oracle at every cell."""
     z = {"fractal": lambda: dem8192, "plane": lambda: demgen.plane(8192, 8192),
          "serpentine_dem": lambda: demgen.serpentine_dem(8192, 8192)}[kind]()
-    d, A = _fused(d8, z, "steepest")
-    d_ref = oracle.flowdir(z)
+    d, A = _fused(d8, z, rule)
+    d_ref = oracle.flowdir(z, rule)
     np.testing.assert_array_equal(d, d_ref)
     np.testing.assert_array_equal(A, oracle.accumulate(d_ref))
     if kind == "serpentine_dem":
         assert A.max() > 8192 * 8192 // 2 - 8192 * 8  # one path of about H*W/2 cells
 
 
-def test_8192_serpentine_dir_field(d8):
-    """One boustrophedon path of 8192^2 cells (about 10^6 tile crossings)."""
+@pytest.mark.parametrize("strategy", ["ring", "jump"])
+def test_8192_serpentine_dir_field(d8, strategy):
+    """One boustrophedon path of 8192^2 cells (about 10^6 tile crossings), with
+    the walks and with pointer jumping (every tile holds one 4096-cell chain)."""
     f = demgen.serpentine_dirs(8192, 8192)
-    A = u32(d8.accumulate(to_dev(f)))
+    d8.set_strategy(strategy)
+    try:
+        A = u32(d8.accumulate(to_dev(f)))
+    finally:
+        d8.set_strategy("ring")
     assert d8.get_status() == "OK"
     np.testing.assert_array_equal(A, oracle.accumulate(f))
     assert A[8191, 0] == 8192 * 8192  # the last cell of the path (odd row ends at col 0)
 
 
-@pytest.mark.parametrize("shape", [(32768, 32768), (16384, 65536)])
-def test_full_size_properties(d8, shape):
-    """The largest configurations: directions against the oracle at every cell,
-    counts by the Eq. 1 recursion at every cell plus conservation (together
-    these fix the counts uniquely)."""
-    H, W = shape
+@pytest.mark.parametrize("rule", RULES)
+def test_32768_fused_full_oracle(d8, rule):
+    """The headline 32768^2 fractal under both rules: directions and counts
+    against the oracle at every one of its 1.07 G cells (the oracle's result
+    is cached beside the DEM), plus the Eq. 1 recursion and conservation on
+    the GPU result."""
+    H = W = 32768
     z = demgen.fractal(H, W)
+    d_ref, A_ref = oracle_cache.flowdir_accumulate(z, f"fractal_{H}x{W}_s{demgen.SEED_BASE}", rule)
     zt = to_dev(z)
-    d, A = d8.flowdir_accumulate(zt, "steepest")
+    d, A = d8.flowdir_accumulate(zt, rule)
     torch.cuda.synchronize()
     assert d8.get_status() == "OK"
     del zt
-    np.testing.assert_array_equal(d.cpu().numpy(), oracle.flowdir(z))
+    assert recursion_residual_gpu(d, A) == 0
+    assert terminal_sum_gpu(d, A) == H * W
+    np.testing.assert_array_equal(d.cpu().numpy(), d_ref)
+    del d
+    np.testing.assert_array_equal(u32(A), A_ref)
+
+
+@pytest.mark.parametrize("rule", RULES)
+def test_65536x16384_properties(d8, rule):
+    """The anisotropic 16384 x 65536 fractal: directions against the oracle at
+    every cell, counts by the Eq. 1 recursion at every cell plus conservation
+    (together these fix the counts uniquely)."""
+    H, W = 16384, 65536
+    z = demgen.fractal(H, W)
+    zt = to_dev(z)
+    d, A = d8.flowdir_accumulate(zt, rule)
+    torch.cuda.synchronize()
+    assert d8.get_status() == "OK"
+    del zt
+    np.testing.assert_array_equal(d.cpu().numpy(), oracle.flowdir(z, rule))
     assert recursion_residual_gpu(d, A) == 0
     assert terminal_sum_gpu(d, A) == H * W

@@ -112,3 +112,23 @@ def test_8192_weighted_forward_backward(d8):
     rhs = float((g.astype(np.float64) * w.astype(np.float64)).sum())
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
     assert d8.get_status() == "OK"
+
+
+@pytest.mark.parametrize("strategy", ["ring", "jump"])
+def test_weighted_top_level_strategies(d8, strategy):
+    """Weighted areas through a top level above the 512-cell groups, solved by
+    the queue walk and by pointer jumping (float-float sums added in another
+    order): both within the bar against fp64, on a fractal DEM and on a
+    serpentine field whose one chain crosses the top level's units."""
+    d8.set_strategy(strategy)
+    try:
+        for f in (oracle.flowdir(demgen.fractal(1500, 1300, seed=31, cache=False)),
+                  demgen.serpentine_dirs(1400, 1200)):
+            H, W = f.shape
+            w = demgen.lognormal_weights(H, W, seed=9)
+            A = d8.accumulate_weighted(to_dev(f), to_dev(w)).cpu().numpy()
+            assert d8.get_status() == "OK"
+            A64 = oracle.accumulate_weighted(f, w.astype(np.float64))
+            assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
+    finally:
+        d8.set_strategy("ring")
