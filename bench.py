@@ -4,25 +4,34 @@ fractal DEM (1.07 G cells), one pipeline call per step (direction stencil,
 tile pass, combine, finalise).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--tile T] [--no-cpu-baseline] [--no-extras]
+                  [--workload NAME] [--tile T] [--strategy S] [--no-cpu-baseline]
+                  [--no-extras]
 
 Prints ONE JSON line (rank 0).  `value` is cells/s with the DEM resident in
-HBM (device-timed with CUDA events, max over ranks); `e2e` is the same metric
-through the public API with pinned host buffers, host->device copy of z and
-device->host copy of the directions and counts inside the timed region;
-`roofline` is the dominant kernel's algorithmic bytes per launch over its
-event-timed duration against the measured HBM copy bandwidth; `cpu_baseline`
-times the CPU oracle on a bounded crop of the same DEM.  On one GPU the line
-also carries `batched` (512 DEMs of uneven sizes in one graph-captured
-persistent pipeline, autotuned tile, beside the same DEMs one call at a time)
-and `fwd_bwd` (weighted forward + backward at 8192 x 8192 beside the plain
-pipeline on the same DEM).  With torchrun (N>1) every rank processes its own
-replica of the workload (independent DEMs, no collective on the data path):
-weak scaling.
+HBM (device-timed with CUDA events, max over ranks).  `e2e` is the same metric
+through the public API with pinned host buffers: every step copies its DEM
+in, runs the call and copies the directions and counts out; steps are
+pipelined (the next DEM's copy in and the previous results' copy out overlap
+the current call, on their own streams), and `e2e.serial` gives the same with
+nothing overlapped.  `roofline` is the dominant kernel's algorithmic bytes per
+launch over its event-timed duration against the measured HBM copy
+bandwidth; `cpu_baseline` times the CPU oracle (one core) and
+`cpu_reference_mt` the multi-core CPU reference (every core this process may
+use) on a bounded crop of the same DEM.  On one GPU the line also carries
+`batched` (512 DEMs of uneven sizes in one graph-captured persistent
+pipeline, tile and strategy autotuned, beside the same DEMs one call at a
+time), `fwd_bwd` (weighted forward + backward at 8192 x 8192 beside the plain
+pipeline on the same DEM) and `workloads` (the other configurations: the
+8192^2 tilted plane, the 8192^2 serpentine as a DEM and as a direction field,
+and the 16384 x 65536 fractal, each with the combine's link-graph statistics
+under the queue walk and under pointer jumping).  With torchrun (N>1) every
+rank processes its own replica of the workload (independent DEMs, no
+collective on the data path): weak scaling.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -47,29 +56,25 @@ WORKLOADS = {
 # reads dir (1) and rewrites A only where inflow from other tiles arrives.
 ALG_BYTES = {"flowdir": 5.0, "tile_up": 5.0}
 PIPE_BYTES = 9.0  # z in (4) + dir out (1) + A out (4) per cell for the whole path
-KERNEL_SOURCE = {"flowdir": "d8_flowdir.cu", "tile_up": "d8_unit.cu", "tile_down": "d8_unit.cu"}
+TRAFFIC_FILE = os.path.join("profiles", "ncu_traffic.json")
 
 
 def measured_traffic(stage: str):
-    """DRAM bytes per cell of a stage's kernel from the committed ncu summary,
-    or None when that kernel's source changed since the capture."""
-    import hashlib
-
-    prof = os.path.join(ROOT, "profiles", "tile_kernels_fractal_8192.md")
-    src = os.path.join(ROOT, "paper_1605_05773_gb300", "csrc", KERNEL_SOURCE.get(stage, ""))
+    """DRAM bytes per cell of a stage's kernel from the committed ncu figures
+    (profiles/ncu_traffic.json), or None when that kernel's source changed
+    since the capture."""
     try:
-        text = open(prof).read().split()
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    except OSError:
+        with open(os.path.join(ROOT, TRAFFIC_FILE)) as f:
+            j = json.load(f)
+        src = j["kernel_source"][stage]
+        with open(os.path.join(ROOT, "paper_1605_05773_gb300", "csrc", src), "rb") as f:
+            sha = hashlib.sha1(f.read()).hexdigest()[:12]
+    except (OSError, ValueError, KeyError):
         return None
-    ok = any(text[k] == "kernel_source_sha1" and text[k + 1] == KERNEL_SOURCE[stage] and text[k + 2] == sha
-             for k in range(len(text) - 2))
-    if not ok:
+    if j.get("kernel_source_sha1", {}).get(src) != sha:
         return None
-    for k in range(len(text) - 2):
-        if text[k] == "scaled_traffic_bytes_per_cell" and text[k + 1] == stage:
-            return float(text[k + 2])
-    return None
+    v = j.get("dram_bytes_per_cell", {}).get(stage)
+    return float(v) if v is not None else None
 
 
 def measured_peaks():
@@ -159,8 +164,53 @@ def barrier(world):
         dist.barrier()
 
 
+# ---- result guards on the timed buffers (plain torch, independent of libd8)
+_DI = (-1, -1, 0, 1, 1, 1, 0, -1)
+_DJ = (0, 1, 1, 1, 0, -1, -1, -1)
+
+
+def recursion_residual(dir, A) -> int:
+    """max |A(p) - 1 - sum of A over the cells draining into p| (Eq. 1) in int64."""
+    import torch
+
+    with torch.no_grad():
+        H, W = dir.shape
+        dpad = torch.full((H + 2, W + 2), 255, dtype=torch.uint8, device=dir.device)
+        dpad[1:-1, 1:-1] = dir
+        Apad = torch.zeros((H + 2, W + 2), dtype=torch.int64, device=dir.device)
+        Apad[1:-1, 1:-1] = A.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        inflow = torch.zeros((H, W), dtype=torch.int64, device=dir.device)
+        for k in range(8):
+            nd = dpad[1 + _DI[k]:1 + _DI[k] + H, 1 + _DJ[k]:1 + _DJ[k] + W]
+            na = Apad[1 + _DI[k]:1 + _DI[k] + H, 1 + _DJ[k]:1 + _DJ[k] + W]
+            inflow += torch.where(nd == ((k + 4) % 8), na, 0)
+            del nd, na
+        return int((Apad[1:-1, 1:-1] - 1 - inflow).abs().max().item())
+
+
+def terminal_sum(dir, A) -> int:
+    """Sum of A over the cells where a path ends (codes 8/9, or a target off the grid)."""
+    import torch
+
+    with torch.no_grad():
+        H, W = dir.shape
+        i = torch.arange(H, device=dir.device).view(H, 1)
+        j = torch.arange(W, device=dir.device).view(1, W)
+        term = dir >= 8
+        for k in range(8):
+            off = ((i + _DI[k] < 0) | (i + _DI[k] >= H)) | ((j + _DJ[k] < 0) | (j + _DJ[k] >= W))
+            term |= (dir == k) & off
+        return int((A.view(torch.int32).to(torch.int64) & 0xFFFFFFFF)[term].sum().item())
+
+
+def guard(dir, A) -> bool:
+    H, W = dir.shape
+    return recursion_residual(dir, A) == 0 and terminal_sum(dir, A) == H * W
+
+
+# ---- CPU baselines
 def oracle_sample(z, side: int):
-    """Time the CPU oracle (directions + queue method) on a side x side crop."""
+    """Time the CPU oracle (directions + queue method, one core) on a side x side crop."""
     import numpy as np
 
     import oracle
@@ -170,6 +220,22 @@ def oracle_sample(z, side: int):
     d = oracle.flowdir(crop)
     oracle.accumulate(d)
     return time.perf_counter() - t0, crop.size
+
+
+def cpuref_sample(z, side: int):
+    """Time the multi-core CPU reference on a side x side crop (median of 3)."""
+    import numpy as np
+
+    import cpuref
+
+    crop = np.ascontiguousarray(z[:side, :side])
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        d = cpuref.flowdir(crop)
+        cpuref.accumulate(d)
+        ts.append(time.perf_counter() - t0)
+    return sorted(ts)[1], crop.size, cpuref.cores()
 
 
 def run_reference(args, world, rank):
@@ -217,17 +283,96 @@ def _event_ms(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
+def run_e2e(lib, z_host, H, W, steps, dev, world):
+    """Directions and counts end to end through the public call, K steps, each
+    step copying its DEM in from pinned host memory and its directions and
+    counts out to pinned host memory.  Pipelined: copies in on one stream,
+    the call on the compute stream, copies out on a third, two device buffer
+    sets alternating, so step k+1's copy in and step k-1's copy out overlap
+    step k's call.  Also timed with everything on one stream (serial)."""
+    import torch
+
+    cells = H * W
+    zh = torch.from_numpy(z_host).pin_memory()
+    dh = [torch.empty((H, W), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    Ah = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(2)]
+    zd = [torch.empty((H, W), dtype=torch.float32, device=dev) for _ in range(2)]
+    dd = [torch.empty((H, W), dtype=torch.uint8, device=dev) for _ in range(2)]
+    Ad = [torch.empty((H, W), dtype=torch.uint32, device=dev) for _ in range(2)]
+    s_in, s_cmp, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+    torch.cuda.synchronize(dev)
+
+    def pipelined(k_steps):
+        copied = [torch.cuda.Event() for _ in range(k_steps)]
+        computed = [torch.cuda.Event() for _ in range(k_steps)]
+        drained = [torch.cuda.Event() for _ in range(k_steps)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s_in)
+        s_cmp.wait_event(e0)
+        s_out.wait_event(e0)
+        for k in range(k_steps):
+            b = k & 1
+            with torch.cuda.stream(s_in):
+                if k >= 2:
+                    s_in.wait_event(computed[k - 2])  # the call of step k-2 is done with zd[b]
+                zd[b].copy_(zh, non_blocking=True)
+                copied[k].record(s_in)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(copied[k])
+                if k >= 2:
+                    s_cmp.wait_event(drained[k - 2])  # dd[b], Ad[b] copied out
+                lib.flowdir_accumulate(zd[b], "steepest", dir=dd[b], A=Ad[b])
+                computed[k].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(computed[k])
+                dh[b].copy_(dd[b], non_blocking=True)
+                Ah[b].copy_(Ad[b].view(torch.int32), non_blocking=True)
+                drained[k].record(s_out)
+        s_in.wait_event(drained[k_steps - 1])
+        e1.record(s_in)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def serial(k_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s_cmp):
+            e0.record(s_cmp)
+            for _ in range(k_steps):
+                zd[0].copy_(zh, non_blocking=True)
+                lib.flowdir_accumulate(zd[0], "steepest", dir=dd[0], A=Ad[0])
+                dh[0].copy_(dd[0], non_blocking=True)
+                Ah[0].copy_(Ad[0].view(torch.int32), non_blocking=True)
+            e1.record(s_cmp)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    pipelined(2)  # warm-up
+    barrier(world)
+    ms_p = max_over_ranks(pipelined(steps), world, dev)
+    barrier(world)
+    ms_s = max_over_ranks(serial(steps), world, dev)
+    ok = guard(dd[(steps - 1) & 1], Ad[(steps - 1) & 1])
+    for t in (zd, dd, Ad):
+        t.clear()
+    return {"value": world * cells * steps / (ms_p / 1e3), "unit": "cells/s", "h2d_bytes_per_step": 4 * cells,
+            "d2h_bytes_per_step": 5 * cells, "steps": steps, "ms_per_step": ms_p / steps,
+            "how": "public call with pinned host buffers; copies in, the call and copies out on three streams, "
+                   "two device buffer sets, consecutive steps overlapped",
+            "parity_guard": ok,
+            "serial": {"value": world * cells * steps / (ms_s / 1e3), "ms_per_step": ms_s / steps,
+                       "how": "the same with copy in, call and copy out back to back on one stream"}}
+
+
 def run_batched(dev, stream, steps: int):
     """The 512-DEM batch (sides log-uniform in [128, 4096], aspect up to 1:4)
-    through the graph-captured persistent pipeline with the autotuned tile,
-    beside the same DEMs run one call at a time."""
+    through the graph-captured persistent pipeline with the autotuned tile and
+    strategy, beside the same DEMs run one call at a time."""
     from concurrent.futures import ThreadPoolExecutor
 
     import torch
 
     import demgen
     import paper_1605_05773_gb300 as lib
-    from tests.gpu_util import recursion_residual_gpu, terminal_sum_gpu
 
     shapes = demgen.batch_shapes(512)
     with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:  # the C generator releases the GIL
@@ -237,7 +382,8 @@ def run_batched(dev, stream, steps: int):
     del zs
     dirs = [torch.empty(s, dtype=torch.uint8, device=dev) for s in shapes]
     As = [torch.empty(s, dtype=torch.uint32, device=dev) for s in shapes]
-    tile, tune_ms = lib.autotune_batch(zt, dirs, As)
+    tile, strat, tune = lib.autotune_batch(zt, dirs, As)
+    table = {str(t): {s: tune[(t, s)] for s in lib.STRATEGIES} for t in (32, 64, 128)}
     plan = lib.BatchPlan(shapes, dev)
     for _ in range(2):
         plan.run(zt, dirs, As)
@@ -245,8 +391,7 @@ def run_batched(dev, stream, steps: int):
     if lib.get_status(dev) != "OK":
         raise RuntimeError("batched run: device status")
     ms = _event_ms(lambda: plan.run(zt, dirs, As), steps, stream)
-    ok = all(recursion_residual_gpu(dirs[k], As[k]) == 0 and terminal_sum_gpu(dirs[k], As[k]) == h * w
-             for k, (h, w) in enumerate(shapes) if k % 32 == 0)
+    ok = all(guard(dirs[k], As[k]) for k in range(0, len(shapes), 32))
 
     def one_by_one():
         for k in range(len(shapes)):
@@ -257,10 +402,12 @@ def run_batched(dev, stream, steps: int):
     plan.close()
     return {"workload": "batch_512", "description": "512 pit-free fractal DEMs, sides log-uniform in [128, 4096], "
                                                     "aspect 1:1-1:4, one graph-captured persistent pipeline",
-            "dems": len(shapes), "cells": cells, "tile": tile, "autotune_ms": tune_ms, "steps": steps,
-            "value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms,
+            "dems": len(shapes), "cells": cells, "tile": tile, "strategy": strat,
+            "autotune_ms": table, "autotune_how": "median of 5 graph replays per (tile, strategy) point",
+            "steps": steps, "value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms,
             "unbatched": {"value": cells / (ms_single / 1e3), "ms_per_step": ms_single,
-                          "how": "the same 512 DEMs through d8_flowdir_accumulate, one call per DEM, same tile"},
+                          "how": "the same 512 DEMs through d8_flowdir_accumulate, one call per DEM, same tile "
+                                 "and strategy"},
             "parity_guard": ok}
 
 
@@ -304,8 +451,57 @@ def run_fwd_bwd(dev, stream, steps: int):
                       "how": "d8_flowdir_accumulate (unit counts, directions included) on the same DEM"}}
 
 
+def run_workloads(dev, stream, steps: int):
+    """The other configurations, each timed under the queue walk (strategy
+    "ring") and under top-level pointer jumping ("jump"), with the combine's
+    link-graph statistics (group levels, top-level exits, and the rounds that
+    bound the depth of the top-level link graph: how far the flow paths wind
+    across the tiles)."""
+    import torch
+
+    import demgen
+    import paper_1605_05773_gb300 as lib
+
+    cases = [
+        ("plane_8192", "8192x8192 tilted plane (0.05 m/cell S, 0.02 m/cell E, +-0.01 m noise) + eps-fill, "
+                       "directions and counts", lambda: demgen.plane(8192, 8192), "z"),
+        ("serpentine_dem_8192", "8192x8192 realisable serpentine DEM (width-1 channels on odd rows, one outlet), "
+                                "directions and counts", lambda: demgen.serpentine_dem(8192, 8192), "z"),
+        ("serpentine_dirs_8192", "8192x8192 boustrophedon direction field: one path through all 2^26 cells, "
+                                 "counts only", lambda: demgen.serpentine_dirs(8192, 8192), "dir"),
+        ("fractal_16384x65536", "16384x65536 pit-free fractal DEM (4x1 lattice of diamond-square squares), "
+                                "directions and counts", lambda: demgen.fractal(16384, 65536), "z"),
+    ]
+    out = {}
+    for name, desc, make, kind in cases:
+        host = make()
+        H, W = host.shape
+        x = torch.from_numpy(host).to(dev)
+        del host
+        d = x if kind == "dir" else torch.empty((H, W), dtype=torch.uint8, device=dev)
+        A = torch.empty((H, W), dtype=torch.uint32, device=dev)
+        call = (lambda: lib.accumulate(d, out=A)) if kind == "dir" else \
+            (lambda: lib.flowdir_accumulate(x, "steepest", dir=d, A=A))
+        entry = {"description": desc, "H": H, "W": W, "cells": H * W}
+        for strat in ("ring", "jump"):
+            lib.set_strategy(strat, dev)
+            call()
+            torch.cuda.synchronize(dev)
+            if lib.get_status(dev) != "OK":
+                raise RuntimeError(f"{name}: device status")
+            stats = lib.combine_stats(dev)
+            reps = steps if W * H <= (1 << 28) else max(2, steps // 2)
+            ms = _event_ms(call, reps, stream)
+            entry[strat] = {"ms_per_step": ms, "value": H * W / (ms / 1e3), "unit": "cells/s", "combine": stats}
+        entry["parity_guard"] = guard(d, A)
+        lib.set_strategy("ring", dev)
+        out[name] = entry
+        del x, d, A
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
 
     import demgen
@@ -317,6 +513,7 @@ def run_ours(args, world, rank, local):
     cells = H * W
     z_host = demgen.fractal(H, W)  # replicas: every rank gets the same recipe
     lib.set_tile(args.tile)
+    lib.set_strategy(args.strategy)
     z = torch.from_numpy(z_host).to(dev)
     d = torch.empty((H, W), dtype=torch.uint8, device=dev)
     A = torch.empty((H, W), dtype=torch.uint32, device=dev)
@@ -349,6 +546,8 @@ def run_ours(args, world, rank, local):
     lib.set_profiling(False, dev)
     ms_max = max_over_ranks(ms, world, dev)
     value = world * cells * args.steps / (ms_max / 1e3)
+    stats = lib.combine_stats(dev)
+    ok = guard(d, A)
 
     # dominant kernel's roofline (algorithmic bytes / event-timed duration)
     peak, peak_kind = measured_peaks()
@@ -358,65 +557,53 @@ def run_ours(args, world, rank, local):
     tb = measured_traffic(dom)
     launches = sum(v[1] for v in stages.values())
 
-    # end to end through the public API: pinned host z in, dirs + counts out
-    e2e_steps = max(1, min(args.steps, 5))
-    zh = torch.from_numpy(z_host).pin_memory()
-    dh = torch.empty((H, W), dtype=torch.uint8).pin_memory()
-    Ah = torch.empty((H, W), dtype=torch.int32).pin_memory()
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for _ in range(e2e_steps):
-        z.copy_(zh, non_blocking=True)
-        lib.flowdir_accumulate(z, "steepest", dir=d, A=A)
-        dh.copy_(d, non_blocking=True)
-        Ah.copy_(A.view(torch.int32), non_blocking=True)
-    f1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = max_over_ranks(f0.elapsed_time(f1), world, dev)
-    e2e_val = world * cells * e2e_steps / (e2e_ms / 1e3)
+    del z
+    torch.cuda.empty_cache()
+    e2e = run_e2e(lib, z_host, H, W, max(3, min(args.steps, 6)), dev, world)
 
     if rank == 0:
-        # correctness guard on the timed buffers: Eq. 1 recursion and conservation
-        from tests.gpu_util import recursion_residual_gpu, terminal_sum_gpu
-
-        ok = recursion_residual_gpu(d, A) == 0 and terminal_sum_gpu(d, A) == cells
-        del z
-        cpu = None
+        cpu = mt = None
         if not args.no_cpu_baseline:
             side = min(H, W, 8192)
             t, n = oracle_sample(z_host, side)
             cpu = {"value": n / t, "unit": "cells/s", "cores": 1, "kind": "oracle",
                    "sample": f"{side}x{side} crop of the workload DEM (oracle directions + one-worker queue method)"}
+            t, n, nc = cpuref_sample(z_host, side)
+            mt = {"value": n / t, "unit": "cells/s", "cores": nc,
+                  "kind": "multi-core CPU reference (OpenMP direction pass + the paper's shared-memory queue method "
+                          "with one queue per thread)",
+                  "sample": f"{side}x{side} crop of the workload DEM, median of 3"}
         line = {
             "metric": "cells_per_second", "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 dirs, u32 counts", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "H": H, "W": W, "tile": args.tile,
+                       "strategy": args.strategy,
                        "l2": "inputs larger than L2 (4.3 GB z per step, 129 MB L2)", "parity_guard": ok},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": (tb * cells if tb else None),
-                         "traffic_note": "ncu dram bytes per cell at 8192^2 (profiles/tile_kernels_fractal_8192.md) x cells; "
-                                         "null when the kernel changed since that capture",
+                         "traffic_note": f"ncu dram bytes per cell at 8192^2 ({TRAFFIC_FILE}) x cells; null when "
+                                         "the kernel changed since that capture",
                          "peak_kind": peak_kind,
                          "alg_bytes_per_cell": ALG_BYTES[dom], "ms_per_launch": dom_ms},
             "pipeline_roofline": {"alg_bytes_per_cell": PIPE_BYTES,
                                   "achieved": PIPE_BYTES * cells / (ms_max / args.steps / 1e3) / 1e9,
                                   "frac": PIPE_BYTES * cells / (ms_max / args.steps / 1e3) / 1e9 / peak},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items() if v[1]},
+            "combine": stats,
             "gpu_launches": launches,
-            "e2e": {"value": e2e_val, "unit": "cells/s", "h2d_bytes_per_step": 4 * cells,
-                    "d2h_bytes_per_step": 5 * cells, "steps": e2e_steps},
+            "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_reference_mt": mt,
             "clocks": clk,
         }
         if world == 1 and not args.no_extras:
             lib.set_profiling(False, dev)
             line["batched"] = run_batched(dev, stream, max(3, min(args.steps, 5)))
             lib.set_tile(args.tile)
+            lib.set_strategy(args.strategy)
             line["fwd_bwd"] = run_fwd_bwd(dev, stream, max(3, min(args.steps, 10)))
+            line["workloads"] = run_workloads(dev, stream, max(3, min(args.steps, 10)))
         print(json.dumps(line), flush=True)
     return 0
 
@@ -429,8 +616,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fractal_32768")
     ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--strategy", choices=["ring", "lane_mask", "jump"], default="ring")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and fwd+bwd lines")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, fwd+bwd and workloads lines")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -146,23 +146,37 @@ d8_status d8_batch_destroy(d8_batch* plan);
 
 /* Autotuner for batches: runs d8_batch_flowdir_accumulate on the given batch
  * (shapes and buffers exactly as for d8_batch_plan and
- * d8_batch_flowdir_accumulate) with every supported tile side (32, 64, 128),
- * one untimed run then two timed graph replays each, and keeps the fastest:
- * *best_tile receives it and the context's tile side is set to it, so a plan
- * made next uses it.  ms: optional host array of 3 floats receiving the
- * per-run milliseconds for tiles 32, 64, 128 (-1 where that tile failed).
- * The paper has no counterpart: its partition size is an input of the method,
- * and here it is chosen by measurement on the target GPU.  dir and A hold the
- * results of the last run.  Synchronises `stream`.
- * Errors: D8_ERR_ARG, or the first error of the runs if every tile failed. */
+ * d8_batch_flowdir_accumulate) at every supported tile side (32, 64, 128)
+ * with every frontier strategy (0, 1, 2; see d8_set_strategy): per point one
+ * untimed run that captures the graph, then 5 graph replays timed one by
+ * one, scored by their median.  The fastest point wins: *best_tile and
+ * *best_strategy (may be NULL) receive it, and the context's tile side and
+ * strategy are set to it, so a plan made next uses them.  ms: optional host
+ * array of 9 floats receiving the medians in milliseconds, tile-major
+ * (ms[3 * t + s] for tile index t = 0, 1, 2 and strategy s), -1 where a point
+ * failed.  The paper has no counterpart: its partition size is an input of the
+ * method, and here it is chosen by measurement on the target GPU.  dir and A
+ * hold the results of the last run.  Synchronises `stream`.
+ * Errors: D8_ERR_ARG, or the first error of the runs if every point failed. */
 d8_status d8_batch_autotune(d8_ctx* ctx, int n, const int64_t* H, const int64_t* W, const float* const* z,
                             uint8_t* const* dir, uint32_t* const* A, d8_rule rule, d8_stream stream, int* best_tile,
-                            float* ms);
+                            int* best_strategy, float* ms);
 
 /* Synchronise `stream`, read and clear the context's device status word.
  * Returns D8_OK or the first device-side error recorded (NONFINITE, ARG,
  * CYCLE, TIMEOUT, in that order of precedence). */
 d8_status d8_get_status(d8_ctx* ctx, d8_stream stream);
+
+/* Link-graph statistics of the combine of the last d8_accumulate,
+ * d8_flowdir_accumulate or d8_accumulate_weighted call on this context
+ * (Algorithms 5-6; the paper's winding of flow paths across partitions):
+ * out[0] = group levels above the tiles, out[1] = units at the top level
+ * (0 when the group levels covered the grid), out[2] = exits in the top
+ * level's link graph, out[3] = pointer-jumping rounds that found work
+ * (strategy 2; the graph's depth is below 2^out[3]) or -1 (queue walk).
+ * out: host array of n >= 4 entries.  Synchronises `stream`.
+ * Errors: D8_ERR_ARG, D8_ERR_CUDA. */
+d8_status d8_combine_stats(d8_ctx* ctx, d8_stream stream, int64_t* out, int n);
 
 /* Static text for a status code. */
 const char* d8_status_string(d8_status s);

@@ -13,6 +13,7 @@ calls raise.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import threading
 
@@ -22,8 +23,8 @@ from . import build as _build
 
 __all__ = [
     "load", "flowdir", "accumulate", "set_strategy", "STRATEGIES", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
-    "weighted_upslope", "WeightedUpslope", "BatchPlan", "autotune_batch", "get_status", "set_tile", "set_profiling",
-    "stage_times", "D8Error", "OUTLET", "SINK", "RULES",
+    "weighted_upslope", "WeightedUpslope", "BatchPlan", "autotune_batch", "shape_class", "get_status", "set_tile", "set_profiling",
+    "stage_times", "combine_stats", "D8Error", "OUTLET", "SINK", "RULES",
 ]
 
 OUTLET, SINK = 8, 9
@@ -83,8 +84,9 @@ def load() -> ctypes.CDLL:
             "d8_batch_destroy": [vp],
             "d8_batch_autotune": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp),
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp, ctypes.POINTER(i32),
-                                  ctypes.POINTER(ctypes.c_float)],
+                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
             "d8_get_status": [vp, vp],
+            "d8_combine_stats": [vp, vp, ctypes.POINTER(i64), i32],
             "d8_set_profiling": [vp, i32],
             "d8_stage_times": [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i64), i32, ctypes.POINTER(i32)],
         }
@@ -263,6 +265,19 @@ def get_status(device=None, stream=None) -> str:
     return STATUS.get(rc, str(rc))
 
 
+def combine_stats(device=None) -> dict:
+    """Link-graph statistics of the last forward call's combine: group levels,
+    top-level units, top-level exits and (strategy "jump") the pointer-jumping
+    rounds that found work, which bound the graph's depth by 2^rounds."""
+    L = load()
+    dev = device if device is not None else torch.cuda.current_device()
+    out = (ctypes.c_int64 * 4)()
+    _check(L.d8_combine_stats(context(dev), ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream), out, 4),
+           "d8_combine_stats")
+    return {"group_levels": int(out[0]), "top_units": int(out[1]), "top_exits": int(out[2]),
+            "top_jump_rounds": int(out[3]) if out[3] >= 0 else None}
+
+
 def check_status(what: str = "device", device=None):
     st = get_status(device)
     if st != "OK":
@@ -284,25 +299,70 @@ def _batch_buffers(shapes, zs, dirs, As, device):
     return dirs, As, ptrs
 
 
-def autotune_batch(zs, dirs=None, As=None, rule: str = "steepest", device=None):
-    """Pick the tile side for a batch by timing the batched pipeline with each
-    (d8_batch_autotune).  Sets the tile for later calls on this device and
-    returns (tile, {tile: ms per run})."""
-    global _tile
+def shape_class(shapes) -> str:
+    """Coarse class of a batch for the autotuner cache: the number of DEMs and
+    the total and largest sizes, each rounded to a power of two."""
+    cells = sum(h * w for h, w in shapes)
+    side = max(max(h, w) for h, w in shapes)
+    return f"n{len(shapes)}_cells2^{max(cells, 1).bit_length() - 1}_side2^{max(side, 1).bit_length() - 1}"
+
+
+def _cache_key(device, shapes, rule) -> str:
+    return f"{torch.cuda.get_device_name(device)}|{shape_class(shapes)}|{rule}"
+
+
+def _read_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def autotune_batch(zs, dirs=None, As=None, rule: str = "steepest", device=None, cache: str | None = None):
+    """Pick the tile side and frontier strategy for a batch by timing the
+    batched pipeline at every (tile, strategy) point (d8_batch_autotune).
+    Sets them for later calls on this device and returns
+    (tile, strategy name, {(tile, strategy name): median ms}).
+
+    cache: optional path of a JSON file keyed by GPU name, the batch's shape
+    class (shape_class) and the rule.  A hit sets the stored choice without
+    timing anything (its timings dict is the stored one); a miss times and
+    stores."""
+    global _tile, _strategy
     L = load()
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     shapes = [tuple(int(x) for x in z.shape) for z in zs]
+    names = {v: k for k, v in STRATEGIES.items()}
+    key = _cache_key(dev, shapes, rule)
+    if cache is not None:
+        hit = _read_cache(cache).get(key)
+        if hit is not None:
+            set_tile(int(hit["tile"]), dev)
+            set_strategy(hit["strategy"], dev)
+            timings = {(int(t), st): float(m) for t, st, m in hit.get("ms", [])}
+            return int(hit["tile"]), hit["strategy"], timings
     n = len(shapes)
     dirs, As, (zp, dp, ap) = _batch_buffers(shapes, zs, dirs, As, dev)
     Hs = (ctypes.c_int64 * n)(*[h for h, _ in shapes])
     Ws = (ctypes.c_int64 * n)(*[w for _, w in shapes])
-    best = ctypes.c_int()
-    ms = (ctypes.c_float * 3)()
+    best, best_s = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_float * 9)()
     _check(L.d8_batch_autotune(context(dev), n, Hs, Ws, zp, dp, ap, RULES[rule],
-                               ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream), ctypes.byref(best), ms),
+                               ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream), ctypes.byref(best),
+                               ctypes.byref(best_s), ms),
            "d8_batch_autotune")
-    _tile = best.value
-    return best.value, {t: float(m) for t, m in zip((32, 64, 128), ms)}
+    _tile, _strategy = best.value, best_s.value
+    timings = {(t, names[s]): float(ms[3 * k + s]) for k, t in enumerate((32, 64, 128)) for s in range(3)}
+    if cache is not None:
+        entries = _read_cache(cache)
+        entries[key] = {"tile": best.value, "strategy": names[best_s.value],
+                        "ms": [[t, st, m] for (t, st), m in timings.items()]}
+        tmp = f"{cache}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(entries, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return best.value, names[best_s.value], timings
 
 
 class BatchPlan:

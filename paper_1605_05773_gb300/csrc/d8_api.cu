@@ -48,6 +48,12 @@ struct d8_ctx {
   std::vector<Timing> pending;
   double ms[ST_COUNT] = {};
   int64_t launches[ST_COUNT] = {};
+  // the last forward call's combine, for d8_combine_stats
+  int last_levels = 0;
+  int64_t last_top_units = 0;
+  bool last_jump = false;
+  uint32_t* last_counters = nullptr;
+  uint32_t* last_flags = nullptr;
 };
 
 struct d8_batch {
@@ -328,6 +334,11 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
       dts[l] = single(dl);
     }
     const HPlan hp = carve_hier(static_cast<char*>(c->ws) + pb, hs, p, dts, weighted);
+    c->last_levels = hs.nlev;
+    c->last_top_units = hs.need_top ? hs.nunits[hs.nlev] : 0;
+    c->last_jump = hp.top.jump;
+    c->last_counters = hs.need_top ? hp.top.counters : nullptr;
+    c->last_flags = hs.need_top ? hp.top.flags : nullptr;
     e = launch_combine_hier(hp, s, &sc.n);
   }
   if (e != cudaSuccess) return cuda_fail(e);
@@ -436,6 +447,31 @@ d8_status d8_stage_times(d8_ctx* c, float* ms, int64_t* launches, int max, int* 
     c->launches[s] = 0;
   }
   if (n) *n = ST_COUNT;
+  return D8_OK;
+}
+
+d8_status d8_combine_stats(d8_ctx* c, d8_stream stream, int64_t* out, int n) {
+  if (!c || !out || n < 4) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  out[0] = c->last_levels;
+  out[1] = c->last_top_units;
+  out[2] = 0;
+  out[3] = -1;
+  if (!c->last_counters) return D8_OK;
+  uint32_t cnt[4] = {}, fl[MAX_ROUNDS + 2] = {};
+  cudaError_t e = cudaMemcpyAsync(cnt, c->last_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && c->last_jump) e = cudaMemcpyAsync(fl, c->last_flags, sizeof(fl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return D8_ERR_CUDA;
+  if (c->last_jump) {
+    out[2] = cnt[0];  // every exit listed
+    int r = 0;
+    while (r < MAX_ROUNDS + 1 && fl[r]) r++;
+    out[3] = r;
+  } else {
+    out[2] = cnt[1];  // exits counted by the source listing
+  }
   return D8_OK;
 }
 
@@ -764,58 +800,81 @@ d8_status d8_batch_destroy(d8_batch* b) {
 
 // Autotuner for batches: the tile side sets how the paper's partitions map
 // onto the GPU (shared memory per tile, tiles per SM, perimeter share, combine
-// depth), and the best one depends on the mix of DEM sizes, so it is measured.
+// depth) and the frontier strategy how the chains of the flow forest are
+// traversed; the best pair depends on the mix of DEM sizes and on how far
+// their channels wind across tiles, so it is measured.  Each point: one run
+// that captures the graph and warms the caches, then AT_REPS replays timed one
+// by one; the point's time is their median.
 d8_status d8_batch_autotune(d8_ctx* c, int n, const int64_t* H, const int64_t* W, const float* const* z,
                             uint8_t* const* dir, uint32_t* const* A, d8_rule rule, d8_stream stream, int* best_tile,
-                            float* ms) {
+                            int* best_strategy, float* ms) {
   if (!c || !best_tile || n < 1 || !H || !W || !z || !dir || !A || (rule != 0 && rule != 1)) return D8_ERR_ARG;
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   static const int kTiles[3] = {32, 64, 128};
-  const int old_T = c->T;
-  int best = -1;
+  constexpr int AT_REPS = 5;
+  const int old_T = c->T, old_S = c->strat;
+  int best = -1, best_st = 0;
   float best_ms = 0.0f;
   d8_status first_err = D8_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    if (e0) cudaEventDestroy(e0);
-    cudaGetLastError();
-    return D8_ERR_CUDA;
+  cudaEvent_t ev[AT_REPS + 1] = {};
+  for (auto& e : ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto& f : ev)
+        if (f) cudaEventDestroy(f);
+      cudaGetLastError();
+      return D8_ERR_CUDA;
+    }
   }
   for (int k = 0; k < 3; k++) {
-    if (ms) ms[k] = -1.0f;
-    c->T = kTiles[k];
-    d8_batch* b = nullptr;
-    d8_status st = d8_batch_plan(c, n, H, W, &b);
-    // one run captures the graph and warms the caches, then two replays are timed
-    if (st == D8_OK) st = d8_batch_flowdir_accumulate(b, z, dir, A, rule, stream);
-    if (st == D8_OK && cudaEventRecord(e0, s) != cudaSuccess) st = D8_ERR_CUDA;
-    for (int r = 0; r < 2 && st == D8_OK; r++) st = d8_batch_flowdir_accumulate(b, z, dir, A, rule, stream);
-    if (st == D8_OK && cudaEventRecord(e1, s) != cudaSuccess) st = D8_ERR_CUDA;
-    if (st == D8_OK && cudaEventSynchronize(e1) != cudaSuccess) st = D8_ERR_CUDA;
-    float t = 0.0f;
-    if (st == D8_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) st = D8_ERR_CUDA;
-    if (b) d8_batch_destroy(b);
-    if (st != D8_OK) {
-      if (first_err == D8_OK) first_err = st;
-      cudaGetLastError();
-      continue;
-    }
-    t *= 0.5f;
-    if (ms) ms[k] = t;
-    if (best < 0 || t < best_ms) {
-      best = kTiles[k];
-      best_ms = t;
+    for (int st = 0; st < STRAT_COUNT; st++) {
+      const int pt = k * STRAT_COUNT + st;
+      if (ms) ms[pt] = -1.0f;
+      c->T = kTiles[k];
+      c->strat = st;
+      d8_batch* b = nullptr;
+      d8_status r = d8_batch_plan(c, n, H, W, &b);
+      if (r == D8_OK) r = d8_batch_flowdir_accumulate(b, z, dir, A, rule, stream);
+      if (r == D8_OK && cudaEventRecord(ev[0], s) != cudaSuccess) r = D8_ERR_CUDA;
+      for (int q = 0; q < AT_REPS && r == D8_OK; q++) {
+        r = d8_batch_flowdir_accumulate(b, z, dir, A, rule, stream);
+        if (r == D8_OK && cudaEventRecord(ev[q + 1], s) != cudaSuccess) r = D8_ERR_CUDA;
+      }
+      if (r == D8_OK && cudaEventSynchronize(ev[AT_REPS]) != cudaSuccess) r = D8_ERR_CUDA;
+      float t[AT_REPS] = {};
+      for (int q = 0; q < AT_REPS && r == D8_OK; q++)
+        if (cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]) != cudaSuccess) r = D8_ERR_CUDA;
+      if (b) d8_batch_destroy(b);
+      if (r != D8_OK) {
+        if (first_err == D8_OK) first_err = r;
+        cudaGetLastError();
+        continue;
+      }
+      for (int i = 1; i < AT_REPS; i++)  // median of the replays
+        for (int j = i; j > 0 && t[j] < t[j - 1]; j--) {
+          const float x = t[j];
+          t[j] = t[j - 1];
+          t[j - 1] = x;
+        }
+      const float med = t[AT_REPS / 2];
+      if (ms) ms[pt] = med;
+      if (best < 0 || med < best_ms) {
+        best = kTiles[k];
+        best_st = st;
+        best_ms = med;
+      }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev) cudaEventDestroy(e);
   if (best < 0) {
     c->T = old_T;
+    c->strat = old_S;
     return first_err == D8_OK ? D8_ERR_CUDA : first_err;
   }
   c->T = best;
+  c->strat = best_st;
   *best_tile = best;
+  if (best_strategy) *best_strategy = best_st;
   return D8_OK;
 }
 

@@ -80,9 +80,10 @@ def test_measured_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypa
     (src_dir / "d8_unit.cu").write_text("// kernel v1\n")
     (src_dir / "d8_flowdir.cu").write_text("// stencil v1\n")
     sha = hashlib.sha1(b"// kernel v1\n").hexdigest()[:12]
-    (tmp_path / "profiles" / "tile_kernels_fractal_8192.md").write_text(
-        f"    kernel_source_sha1 d8_unit.cu {sha}\n    kernel_source_sha1 d8_flowdir.cu 000000000000\n"
-        "    scaled_traffic_bytes_per_cell tile_up 4.48\n    scaled_traffic_bytes_per_cell flowdir 4.79\n")
+    (tmp_path / bench.TRAFFIC_FILE).write_text(json.dumps({
+        "kernel_source": {"tile_up": "d8_unit.cu", "flowdir": "d8_flowdir.cu"},
+        "kernel_source_sha1": {"d8_unit.cu": sha, "d8_flowdir.cu": "000000000000"},
+        "dram_bytes_per_cell": {"tile_up": 4.48, "flowdir": 4.79}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_traffic("tile_up") == 4.48
     assert bench.measured_traffic("flowdir") is None  # hash differs: stale capture

@@ -54,19 +54,26 @@ def test_batch_512_dems(d8):
     plan.close()
 
 
-def test_autotune_picks_a_tile_and_keeps_results_exact(d8):
-    """The autotuner times the batch with every tile side, leaves the fastest
-    set, and every candidate produces the oracle's results."""
+def test_autotune_picks_a_tile_and_strategy_and_keeps_results_exact(d8, tmp_path):
+    """The autotuner times the batch at every (tile side, strategy) point,
+    leaves the fastest set, stores it in its cache (a second call reads the
+    cache and times nothing), and the chosen pair produces the oracle's
+    results.  The batch holds a serpentine field's DEM version too, so the
+    chain-heavy case is among the inputs."""
     shapes = [(200, 300), (513, 129), (64, 64), (1000, 257), (129, 700)]
     zs = [demgen.fractal(h, w, seed=300 + k, cache=False) for k, (h, w) in enumerate(shapes)]
+    zs.append(demgen.serpentine_dem(1200, 700))
+    shapes.append((1200, 700))
     zt = [to_dev(z) for z in zs]
+    cache = str(tmp_path / "autotune.json")
     try:
-        tile, ms = d8.autotune_batch(zt)
-        assert tile in (32, 64, 128)
-        assert set(ms) == {32, 64, 128} and all(v > 0 for v in ms.values())
-        assert ms[tile] == min(ms.values())
-        # the last tuning run (tile 128) left its results in the buffers it made;
-        # a plan made now uses the chosen tile
+        tile, strat, ms = d8.autotune_batch(zt, cache=cache)
+        assert tile in (32, 64, 128) and strat in d8.STRATEGIES
+        assert set(ms) == {(t, s) for t in (32, 64, 128) for s in d8.STRATEGIES}
+        assert all(v > 0 for v in ms.values())
+        assert ms[(tile, strat)] == min(ms.values())
+        tile2, strat2, ms2 = d8.autotune_batch(zt, cache=cache)  # a cache hit
+        assert (tile2, strat2) == (tile, strat) and ms2 == ms
         plan = d8.BatchPlan(shapes)
         dirs, As = plan.run(zt)
         torch.cuda.synchronize()
@@ -78,3 +85,4 @@ def test_autotune_picks_a_tile_and_keeps_results_exact(d8):
         plan.close()
     finally:
         d8.set_tile(64)
+        d8.set_strategy("ring")
