@@ -51,6 +51,7 @@ def _configure(lib):
     lib.oracle_accumulate_f64.argtypes = [vp, i64, i64, vp, vp, vp]
     lib.oracle_accumulate_u64.argtypes = [vp, i64, i64, vp]
     lib.oracle_transposed_f64.argtypes = [vp, i64, i64, vp, vp]
+    lib.oracle_fill_eps.argtypes = [vp, i64, i64, ctypes.c_float, vp]
     return lib
 
 
@@ -160,3 +161,17 @@ def transposed(dir: np.ndarray, c: np.ndarray) -> np.ndarray:
     if rc:
         raise OracleError(rc, "transposed")
     return G
+
+
+def fill_eps(z: np.ndarray, eps: float = 1e-3) -> np.ndarray:
+    """Pit and flat removal by epsilon filling (priority flood from the edge):
+    the unique surface with F = z on the edge and, inside, F(c) = z(c) where z
+    is above the lowest neighbouring F, else that F raised by eps (at least
+    one fp32 step).  float32 in and out."""
+    z = _c(z, np.float32)
+    H, W = z.shape
+    F = np.empty((H, W), dtype=np.float32)
+    rc = _load().oracle_fill_eps(z.ctypes.data, H, W, np.float32(eps), F.ctypes.data)
+    if rc:
+        raise OracleError(rc, "fill_eps")
+    return F

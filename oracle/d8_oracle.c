@@ -256,3 +256,105 @@ int oracle_transposed_f64(const uint8_t* dir, int64_t H, int64_t W, const double
   free(order);
   return rc;
 }
+
+/* ---- Pit and flat removal (the method's precondition, "The Algorithm",
+ * first paragraph: the DEM has had its pits raised or drilled and its flats
+ * resolved, so that every interior cell drains).
+ *
+ * Reading taken: epsilon filling.  The filled surface F is the unique array
+ * with F = z on the grid's edge cells and, for every interior cell c, with
+ * m = the smallest F among its eight neighbours,
+ *     F(c) = z(c)      if z(c) > m,
+ *     F(c) = up(m)     otherwise,     up(x) = max(fl32(x + eps), next fp32 above x).
+ * Every interior cell of F has a strictly lower neighbour.  The map is
+ * monotone and raises strictly, so the array is unique; a priority flood
+ * from the edge (cells leave a min-heap in order of F, and a cell first
+ * reached from a cell p gets z if z is above F(p), else up(F(p))) meets every
+ * cell first from its lowest neighbour and so produces exactly that array.
+ * That priority flood is what this function runs: a binary heap ordered by
+ * (F, cell index), one worker, fp32 arithmetic, no contraction. */
+typedef struct {
+  float f;
+  int64_t c;
+} fill_item;
+
+static int fill_less(fill_item a, fill_item b) { return a.f < b.f || (a.f == b.f && a.c < b.c); }
+
+static void heap_push(fill_item* h, int64_t* n, fill_item x) {
+  int64_t i = (*n)++;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (!fill_less(x, h[p])) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i] = x;
+}
+
+static fill_item heap_pop(fill_item* h, int64_t* n) {
+  fill_item top = h[0], x = h[--(*n)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, m = i;
+    fill_item best = x;
+    if (l < *n && fill_less(h[l], best)) {
+      m = l;
+      best = h[l];
+    }
+    if (r < *n && fill_less(h[r], best)) m = r;
+    if (m == i) break;
+    h[i] = h[m];
+    i = m;
+  }
+  if (*n > 0) h[i] = x;
+  return top;
+}
+
+static float fill_up(float x, float eps) {
+  float a = x + eps;
+  float b = nextafterf(x, INFINITY);
+  return a > b ? a : b;
+}
+
+/* F from z (both H x W, row-major).  Returns OR_OK, OR_ERR_NONFINITE (F is
+ * then unspecified), OR_ERR_NOMEM or OR_ERR_ARG. */
+int oracle_fill_eps(const float* z, int64_t H, int64_t W, float eps, float* F) {
+  if (!z || !F || H < 1 || W < 1 || !(eps >= 0.0f)) return OR_ERR_ARG;
+  int64_t N = H * W;
+  for (int64_t c = 0; c < N; c++)
+    if (!isfinite(z[c])) return OR_ERR_NONFINITE;
+  uint8_t* closed = (uint8_t*)calloc((size_t)N, 1);
+  fill_item* h = (fill_item*)malloc(sizeof(fill_item) * (size_t)N);
+  if (!closed || !h) {
+    free(closed);
+    free(h);
+    return OR_ERR_NOMEM;
+  }
+  int64_t n = 0;
+  for (int64_t i = 0; i < H; i++)
+    for (int64_t j = 0; j < W; j++)
+      if (i == 0 || j == 0 || i == H - 1 || j == W - 1) {
+        int64_t c = i * W + j;
+        F[c] = z[c];
+        closed[c] = 1;
+        fill_item it = {F[c], c};
+        heap_push(h, &n, it);
+      }
+  while (n > 0) {
+    fill_item p = heap_pop(h, &n);
+    int64_t pi = p.c / W, pj = p.c % W;
+    for (int k = 0; k < 8; k++) {
+      int64_t i = pi + ODI[k], j = pj + ODJ[k];
+      if (i < 0 || j < 0 || i >= H || j >= W) continue;
+      int64_t c = i * W + j;
+      if (closed[c]) continue;
+      closed[c] = 1;
+      F[c] = z[c] > p.f ? z[c] : fill_up(p.f, eps);
+      fill_item it = {F[c], c};
+      heap_push(h, &n, it);
+    }
+  }
+  free(closed);
+  free(h);
+  return OR_OK;
+}

@@ -26,6 +26,14 @@ MUTATIONS = {
     "adjoint_wrong_order": ("for (int64_t t = N - 1; t >= 0; t--) {", "for (int64_t t = 0; t < N; t++) {"),
     # the lowest rule keeps the HIGHEST lower neighbour
     "lowest_inverted": ("if (zn < best) {", "if (zn < zc && (best == zc || zn > best)) {"),
+    # the fill keeps a cell level with its lowest neighbour (flats not resolved)
+    "fill_keeps_flats": ("F[c] = z[c] > p.f ? z[c] : fill_up(p.f, eps);",
+                         "F[c] = z[c] >= p.f ? z[c] : fill_up(p.f, eps);"),
+    # the raise loses its one-step minimum (x + eps can round back to x)
+    "fill_no_min_step": ("return a > b ? a : b;", "return a;"),
+    # the flood pops the HIGHEST cell first
+    "fill_heap_inverted": ("return a.f < b.f || (a.f == b.f && a.c < b.c);",
+                           "return a.f > b.f || (a.f == b.f && a.c < b.c);"),
 }
 
 PINS = [
@@ -36,6 +44,8 @@ PINS = [
     pins.test_cone_rays,
     pins.test_weighted_matches_bruteforce_and_linearity,
     pins.test_transposed_adjoint_identity_and_bruteforce,
+    pins.test_fill_golden_cases,
+    pins.test_fill_matches_iteration_on_tiny_grids,
 ]
 
 

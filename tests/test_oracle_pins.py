@@ -304,3 +304,93 @@ def test_transposed_central_differences():
         Lm = float((c * oracle.accumulate_weighted(d, w - e)).sum())
         fd = (Lp - Lm) / 2.0
         assert abs(fd - G.ravel()[q]) <= 1e-9 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------ epsilon fill
+def _fill_fixed_point_residual(z, F, eps):
+    """Cells where F breaks the fill's defining equations (an independent
+    restatement of them in numpy): F = z on the edge; inside, with m the
+    lowest of the 8 neighbouring F, F = z if z > m else max(m + eps, next fp32
+    above m)."""
+    z = z.astype(np.float32)
+    H, W = z.shape
+    bad = np.zeros((H, W), dtype=bool)
+    edge = np.zeros((H, W), dtype=bool)
+    edge[0, :] = edge[-1, :] = edge[:, 0] = edge[:, -1] = True
+    bad |= edge & (F != z)
+    if H >= 3 and W >= 3:
+        Fp = np.pad(F, 1, constant_values=np.inf)
+        m = np.full((H, W), np.inf, dtype=np.float32)
+        for di in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                if di or dj:
+                    m = np.minimum(m, Fp[1 + di:1 + di + H, 1 + dj:1 + dj + W])
+        up = np.maximum((m + np.float32(eps)).astype(np.float32), np.nextafter(m, np.float32(np.inf)))
+        want = np.where(z > m, z, up)
+        bad |= ~edge & (F != want)
+    return bad
+
+
+def _fill_by_iteration(z, eps):
+    """Brute force for tiny grids: start from +inf inside and apply the
+    defining equations to every interior cell until nothing changes (a
+    different algorithm from the oracle's priority flood)."""
+    z = z.astype(np.float32)
+    H, W = z.shape
+    F = np.full((H, W), np.inf, dtype=np.float32)
+    F[0, :], F[-1, :], F[:, 0], F[:, -1] = z[0, :], z[-1, :], z[:, 0], z[:, -1]
+    for _ in range(10 * H * W):
+        changed = False
+        for i in range(1, H - 1):
+            for j in range(1, W - 1):
+                m = min(F[i + di, j + dj] for di in (-1, 0, 1) for dj in (-1, 0, 1) if di or dj)
+                m = np.float32(m)
+                v = z[i, j] if z[i, j] > m else max(np.float32(m + np.float32(eps)), np.nextafter(m, np.float32(np.inf)))
+                if v != F[i, j]:
+                    F[i, j] = v
+                    changed = True
+        if not changed:
+            return F
+    raise AssertionError("iteration did not settle")
+
+
+def test_fill_golden_cases():
+    g = named("fill_cases.txt")
+    for name in ("bowl", "plateau", "spill", "keep", "step"):
+        rows = g[name]
+        eps = float(rows[0][0])
+        z = grid(rows[1:], np.float32)
+        F = oracle.fill_eps(z, eps)
+        np.testing.assert_array_equal(F, grid(g[name + "_F"], np.float32), err_msg=name)
+
+
+def test_fill_matches_iteration_on_tiny_grids():
+    rng = np.random.default_rng(1605)
+    for k in range(30):
+        H, W = int(rng.integers(1, 8)), int(rng.integers(1, 9))
+        z = rng.integers(0, 5, size=(H, W)).astype(np.float32)  # many ties and flats
+        eps = [0.25, 0.001, 0.0][k % 3]
+        np.testing.assert_array_equal(oracle.fill_eps(z, eps), _fill_by_iteration(z, eps), err_msg=f"case {k}")
+
+
+def test_fill_defining_equations_and_properties():
+    cases = [demgen.fractal_raw(257, 300, 5), demgen.fractal_raw(129, 65, 6),
+             np.random.default_rng(3).random((97, 131)).astype(np.float32) * 10]
+    for z in cases:
+        F = oracle.fill_eps(z, 1e-3)
+        assert not _fill_fixed_point_residual(z, F, 1e-3).any()
+        assert (F >= z).all()
+        # every interior cell drains: it has a strictly lower neighbour, so the
+        # steepest and lowest rules give no SINK
+        for rule in RULES:
+            assert not (oracle.flowdir(F, rule) == 9).any()
+        np.testing.assert_array_equal(oracle.fill_eps(F, 1e-3), F)  # idempotent
+    z = demgen.fractal(200, 180, seed=8, cache=False)  # already drains everywhere: unchanged
+    np.testing.assert_array_equal(oracle.fill_eps(z, 1e-3), z)
+
+
+def test_fill_rejects_nonfinite():
+    z = np.zeros((5, 5), dtype=np.float32)
+    z[2, 2] = np.nan
+    with pytest.raises(oracle.OracleError):
+        oracle.fill_eps(z)
