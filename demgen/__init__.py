@@ -155,6 +155,15 @@ def plane(H: int, W: int, seed: int = SEED_BASE + 1, cache: bool = True) -> np.n
     return _cached(f"plane_{H}x{W}_s{seed}", make) if cache else make()
 
 
+def plane_raw(H: int, W: int, seed: int = SEED_BASE + 1) -> np.ndarray:
+    """The tilted plane with its +-0.01 m noise, before the fill (it has pits)."""
+    z = np.empty((H, W), dtype=np.float32)
+    rc = _load().demgen_plane(_ptr(z), H, W, seed, 0.05, 0.02, 0.01)
+    if rc:
+        raise RuntimeError("demgen_plane failed")
+    return z
+
+
 def plane_exact(H: int, W: int, sy: float = 1.0, sx: float = 0.0) -> np.ndarray:
     """Noise-free plane z = sy*(H-1-i) + sx*(W-1-j) (no fill)."""
     z = np.empty((H, W), dtype=np.float32)

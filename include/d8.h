@@ -42,7 +42,7 @@ typedef enum {
   D8_ERR_CYCLE = 4,     /* device: the direction field contains a cycle */
   D8_ERR_NOMEM = 5,     /* workspace allocation failed */
   D8_ERR_CUDA = 6,      /* a CUDA runtime call failed */
-  D8_ERR_TIMEOUT = 7,   /* device: a bounded wait gave up */
+  D8_ERR_TIMEOUT = 7,   /* an iteration bound was reached (d8_fill) */
   D8_ERR_CAPACITY = 8   /* grid larger than the fixed scratch of d8_flowdir_accumulate_noalloc */
 } d8_status;
 
@@ -126,6 +126,26 @@ d8_status d8_accumulate_weighted(d8_ctx* ctx, const uint8_t* dir, int64_t H, int
  * accumulation.  Errors as d8_accumulate. */
 d8_status d8_accumulate_backward(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
                                  const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream);
+
+/* Pit and flat removal by epsilon filling, the precondition of the method
+ * ("The Algorithm", first paragraph: pits raised and flats resolved, so that
+ * every interior cell has a strictly lower neighbour).  F is the unique
+ * surface with F = z on the grid's edge and, for every interior cell c with
+ * m = the lowest of its 8 neighbouring F values, F(c) = z(c) if z(c) > m,
+ * else F(c) = max(fl32(m + eps), the next fp32 value above m); it is the
+ * result of a priority flood from the edge that raises each cell reached
+ * from a cell no lower than it to eps above that cell.
+ * z: H x W fp32 elevations (ld ldz); F: H x W fp32 output (ld ldF), must
+ * not overlap z; eps >= 0 (0 raises by one fp32 step).  rounds: optional
+ * host pointer receiving the number of tile rounds the fill took (how far
+ * the filled surface's dependencies wind across the 64 x 64 tiles).
+ * Non-finite z sets D8_ERR_NONFINITE in the status word (F is then
+ * unspecified).  The call synchronises `stream` (it checks for convergence
+ * on the host every 16 rounds).
+ * Errors: D8_ERR_ARG, D8_ERR_NOMEM, D8_ERR_CUDA, D8_ERR_TIMEOUT (not settled
+ * after 2^20 rounds). */
+d8_status d8_fill(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, float eps, float* F,
+                  int64_t ldF, int64_t* rounds, d8_stream stream);
 
 /* Plan a batch of n independent DEMs with the given shapes (host arrays of n
  * entries; DEM k is H[k] x W[k], dense, ld = W[k]).  The plan owns a tile

@@ -22,7 +22,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "load", "flowdir", "accumulate", "set_strategy", "STRATEGIES", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
+    "load", "fill", "flowdir", "accumulate", "set_strategy", "STRATEGIES", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
     "weighted_upslope", "WeightedUpslope", "BatchPlan", "autotune_batch", "shape_class", "get_status", "set_tile", "set_profiling",
     "stage_times", "combine_stats", "D8Error", "OUTLET", "SINK", "RULES",
 ]
@@ -86,6 +86,7 @@ def load() -> ctypes.CDLL:
                                   ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp, ctypes.POINTER(i32),
                                   ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
             "d8_get_status": [vp, vp],
+            "d8_fill": [vp, vp, i64, i64, i64, ctypes.c_float, vp, i64, ctypes.POINTER(i64), vp],
             "d8_combine_stats": [vp, vp, ctypes.POINTER(i64), i32],
             "d8_set_profiling": [vp, i32],
             "d8_stage_times": [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i64), i32, ctypes.POINTER(i32)],
@@ -186,6 +187,19 @@ def flowdir(z: torch.Tensor, rule: str = "steepest", out: torch.Tensor | None = 
     _check(load().d8_flowdir(context(z.device), z.data_ptr(), H, W, ldz, d.data_ptr(), ldd, RULES[rule], _stream(z)),
            "d8_flowdir")
     return d
+
+
+def fill(z: torch.Tensor, eps: float = 1e-3, out: torch.Tensor | None = None, return_rounds: bool = False):
+    """Pit and flat removal by epsilon filling (d8_fill): every interior cell
+    of the result has a strictly lower neighbour.  Synchronises the stream."""
+    H, W, ldz = _grid(z, torch.float32, "z")
+    F = torch.empty((H, W), dtype=torch.float32, device=z.device) if out is None else out
+    _, _, ldf = _grid(F, torch.float32, "out")
+    _same_shape(z, F, "z/out")
+    r = ctypes.c_int64()
+    _check(load().d8_fill(context(z.device), z.data_ptr(), H, W, ldz, float(eps), F.data_ptr(), ldf,
+                          ctypes.byref(r), _stream(z)), "d8_fill")
+    return (F, r.value) if return_rounds else F
 
 
 def accumulate(dir: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:

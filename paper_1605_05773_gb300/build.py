@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libd8.so")
-SOURCES = ["d8_flowdir.cu", "d8_unit.cu", "d8_combine.cu", "d8_fwd.cu", "d8_bwd.cu", "d8_api.cu", "d8_noalloc.cu"]
+SOURCES = ["d8_flowdir.cu", "d8_unit.cu", "d8_combine.cu", "d8_fwd.cu", "d8_bwd.cu", "d8_fill.cu", "d8_api.cu", "d8_noalloc.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

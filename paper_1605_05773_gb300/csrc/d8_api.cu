@@ -14,9 +14,9 @@ using namespace d8;
 
 namespace {
 
-enum Stage { ST_FLOWDIR = 0, ST_UP, ST_COMBINE, ST_DOWN, ST_BWD_UP, ST_BWD_COMBINE, ST_BWD_DOWN, ST_COUNT };
+enum Stage { ST_FLOWDIR = 0, ST_UP, ST_COMBINE, ST_DOWN, ST_BWD_UP, ST_BWD_COMBINE, ST_BWD_DOWN, ST_FILL, ST_COUNT };
 const char* const kStageNames[ST_COUNT] = {"flowdir", "tile_up", "combine", "tile_down",
-                                           "bwd_tile_up", "bwd_combine", "bwd_tile_down"};
+                                           "bwd_tile_up", "bwd_combine", "bwd_tile_down", "fill"};
 
 struct Timing {
   int stage;
@@ -591,6 +591,30 @@ d8_status d8_accumulate_backward(d8_ctx* c, const uint8_t* dir, int64_t H, int64
     e = launch_bwd_down(dt, p, s, &sc.n);
   }
   return cuda_fail(e);
+}
+
+d8_status d8_fill(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, float eps, float* F, int64_t ldF,
+                  int64_t* rounds, d8_stream stream) {
+  if (!c || bad_grid(z, H, W, ldz) || bad_grid(F, H, W, ldF) || !(eps >= 0.0f) || !(eps < INFINITY))
+    return D8_ERR_ARG;
+  // the output must not overlap the input (the fill reads z throughout)
+  const char *zb = reinterpret_cast<const char*>(z), *ze = zb + ((H - 1) * ldz + W) * sizeof(float);
+  const char *fb = reinterpret_cast<const char*>(F), *fe = fb + ((H - 1) * ldF + W) * sizeof(float);
+  if (zb < fe && fb < ze) return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  d8_status st = ensure_ws(c, fill_ws_bytes(H, W));
+  if (st != D8_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int64_t r = 0;
+  bool timed_out = false;
+  cudaError_t e;
+  {
+    StageScope sc(c, ST_FILL, s);
+    e = run_fill(z, H, W, ldz, eps, F, ldF, c->ws, c->status, s, (int64_t)1 << 20, &r, &timed_out, &sc.n);
+  }
+  if (rounds) *rounds = r;
+  if (e != cudaSuccess) return cuda_fail(e);
+  return timed_out ? D8_ERR_TIMEOUT : D8_OK;
 }
 
 // ---------------------------------------------------------------------------

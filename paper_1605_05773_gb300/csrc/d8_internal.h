@@ -122,6 +122,12 @@ cudaError_t launch_combine_hier(const HPlan& hp, cudaStream_t s, int* nlaunch);
 cudaError_t launch_up_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s);
 cudaError_t launch_down_unit(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s);
 
+// ---- pit and flat removal (d8_fill.cu)
+size_t fill_ws_bytes(int64_t H, int64_t W);
+cudaError_t run_fill(const float* z, int64_t H, int64_t W, int64_t ldz, float eps, float* F, int64_t ldF, void* ws,
+                     uint32_t* status, cudaStream_t s, int64_t max_rounds, int64_t* rounds_out, bool* timed_out,
+                     int* nlaunch);
+
 // shared-memory bytes of the per-tile kernels (0 = configuration unsupported)
 size_t up_smem_bytes(int T, int mode);
 size_t down_smem_bytes(int T, bool weighted);
