@@ -24,7 +24,8 @@ time), `fwd_bwd` (weighted forward + backward at 8192 x 8192 beside the plain
 pipeline on the same DEM) and `workloads` (the other configurations: the
 8192^2 tilted plane, the 8192^2 serpentine as a DEM and as a direction field,
 and the 16384 x 65536 fractal, each with the combine's link-graph statistics
-under the queue walk and under pointer jumping).  With torchrun (N>1) every
+under the queue walk and under pointer jumping), and `fill` (pit and flat
+removal on the raw 8192^2 and 32768^2 fractals).  With torchrun (N>1) every
 rank processes its own replica of the workload (independent DEMs, no
 collective on the data path): weak scaling.
 """
@@ -451,6 +452,45 @@ def run_fwd_bwd(dev, stream, steps: int):
                       "how": "d8_flowdir_accumulate (unit counts, directions included) on the same DEM"}}
 
 
+def run_fill(dev, steps: int):
+    """Pit and flat removal (d8_fill) on the raw 8192^2 and 32768^2 fractals
+    (the generator's diamond-square output before its own fill), beside the
+    oracle's priority flood on one host core over a 2048^2 crop."""
+    import numpy as np
+    import torch
+
+    import demgen
+    import oracle
+    import paper_1605_05773_gb300 as lib
+
+    out = {}
+    for n, reps in ((8192, max(2, steps)), (32768, 2)):
+        z = demgen.fractal_raw(n, n, demgen.SEED_BASE)
+        zt = torch.from_numpy(z).to(dev)
+        F = torch.empty_like(zt)
+        lib.fill(zt, 1e-3, out=F)
+        torch.cuda.synchronize(dev)
+        if lib.get_status(dev) != "OK":
+            raise RuntimeError("fill: device status")
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, rounds = lib.fill(zt, 1e-3, out=F, return_rounds=True)
+        torch.cuda.synchronize(dev)
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+        raised = int((F != zt).sum().item())
+        out[f"fractal_raw_{n}"] = {"ms_per_fill": ms, "value": n * n / (ms / 1e3), "unit": "cells/s",
+                                   "tile_rounds": rounds, "cells_raised": raised,
+                                   "timing": "host wall clock around the synchronous call (it checks convergence "
+                                             "on the host every 16 rounds)"}
+        del zt, F
+    crop = np.ascontiguousarray(demgen.fractal_raw(2048, 2048, demgen.SEED_BASE))
+    t0 = time.perf_counter()
+    oracle.fill_eps(crop, 1e-3)
+    out["cpu_oracle_2048"] = {"value": crop.size / (time.perf_counter() - t0), "unit": "cells/s", "cores": 1,
+                              "kind": "oracle (priority flood with a binary heap)"}
+    return out
+
+
 def run_workloads(dev, stream, steps: int):
     """The other configurations, each timed under the queue walk (strategy
     "ring") and under top-level pointer jumping ("jump"), with the combine's
@@ -604,6 +644,7 @@ def run_ours(args, world, rank, local):
             lib.set_strategy(args.strategy)
             line["fwd_bwd"] = run_fwd_bwd(dev, stream, max(3, min(args.steps, 10)))
             line["workloads"] = run_workloads(dev, stream, max(3, min(args.steps, 10)))
+            line["fill"] = run_fill(dev, 3)
         print(json.dumps(line), flush=True)
     return 0
 

@@ -64,7 +64,8 @@ __global__ void k_fill_init(const float* z, int64_t H, int64_t W, int64_t ldz, f
 // count: tiles marked for the next round by this round.
 __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, int64_t W, int64_t ldz, float* F,
                                                     int64_t ldF, float eps, int64_t ntx, int64_t nty,
-                                                    uint8_t* act_cur, uint8_t* act_next, uint32_t* count) {
+                                                    uint8_t* act_cur, uint8_t* act_next, uint8_t* settled,
+                                                    uint32_t* count) {
   extern __shared__ __align__(16) unsigned char sm[];
   float* Fh = reinterpret_cast<float*>(sm + Layout::off_f);
   float* zt = reinterpret_cast<float*>(sm + Layout::off_z);
@@ -85,7 +86,11 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
       if (gi >= 0 && gj >= 0 && gi < H && gj < W && hi <= th && hj <= tw) v = __ldcg(&F[gi * ldF + gj]);
       Fh[q] = v;
     }
-    // z, and the first wave: every interior grid cell of the tile
+    // z, and the first wave: every interior grid cell of the tile on its
+    // first visit; on later visits, when the tile was left at a fixed point
+    // of its halo and only the halo can have changed since, the cells next
+    // to the halo (the tile's border ring)
+    const bool ring_only = settled[t] != 0;
     for (int q = threadIdx.x; q < T * T; q += NTF) {
       const int i = q / T, j = q % T;
       zt[q] = (i < th && j < tw) ? z[(i0 + i) * ldz + (j0 + j)] : 0.0f;
@@ -95,9 +100,11 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
       const int64_t gi = i0 + i;
       uint32_t bits = 0u;
       if (i < th && gi > 0 && gi < H - 1) {
+        const bool row_ring = i == 0 || i == th - 1;
         for (int b = 0; b < 32; b++) {
           const int64_t gj = j0 + jb + b;
-          if (jb + b < tw && gj > 0 && gj < W - 1) bits |= 1u << b;
+          const bool ring = row_ring || jb + b == 0 || jb + b == tw - 1;
+          if (jb + b < tw && gj > 0 && gj < W - 1 && (ring || !ring_only)) bits |= 1u << b;
         }
       }
       mk0[q] = bits;
@@ -162,9 +169,12 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
           marked++;
         }
       }
-      if (wave >= MAX_WAVES) {  // not settled within the cap: visit it again
+      if (wave >= MAX_WAVES) {  // not settled within the cap: visit it again, every cell
         act_next[t] = 1;
+        settled[t] = 0;
         marked++;
+      } else {
+        settled[t] = 1;
       }
       if (marked) atomicAdd(count, marked);
     }
@@ -175,7 +185,7 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
 
 size_t fill_ws_bytes(int64_t H, int64_t W) {
   const int64_t ntiles = ((H + fill::T - 1) / fill::T) * ((W + fill::T - 1) / fill::T);
-  return (size_t)2 * ntiles + 256 + sizeof(uint32_t) * 64;
+  return (size_t)3 * ntiles + 256 + sizeof(uint32_t) * 64;
 }
 
 // The fill: init, then rounds until one marks nothing.  The host reads the
@@ -187,7 +197,8 @@ cudaError_t run_fill(const float* z, int64_t H, int64_t W, int64_t ldz, float ep
   using namespace fill;
   const int64_t ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   uint8_t* act[2] = {static_cast<uint8_t*>(ws), static_cast<uint8_t*>(ws) + ntiles};
-  uint32_t* counts = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + ((2 * ntiles + 255) / 256) * 256);
+  uint8_t* settled = static_cast<uint8_t*>(ws) + 2 * ntiles;
+  uint32_t* counts = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + ((3 * ntiles + 255) / 256) * 256);
   constexpr int CHUNK = 16;  // rounds between host checks; counts[r % CHUNK]
   *timed_out = false;
   int dev = 0, sms = 1, per_sm = 1;
@@ -204,6 +215,7 @@ cudaError_t run_fill(const float* z, int64_t H, int64_t W, int64_t ldz, float ep
   if (grid > ntiles) grid = ntiles;
   e = cudaMemsetAsync(act[0], 1, (size_t)ntiles, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(act[1], 0, (size_t)ntiles, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(settled, 0, (size_t)ntiles, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * CHUNK, s);
   if (e != cudaSuccess) return e;
   int64_t nb = (H * W + 255) / 256;
@@ -214,7 +226,7 @@ cudaError_t run_fill(const float* z, int64_t H, int64_t W, int64_t ldz, float ep
   for (;;) {
     for (int k = 0; k < CHUNK; k++, r++) {
       k_fill_round<<<(unsigned)grid, NTF, Layout::bytes, s>>>(z, H, W, ldz, F, ldF, eps, ntx, nty, act[r & 1],
-                                                              act[(r + 1) & 1], counts + (r % CHUNK));
+                                                              act[(r + 1) & 1], settled, counts + (r % CHUNK));
       ++*nlaunch;
     }
     uint32_t h[CHUNK];
