@@ -47,6 +47,7 @@ struct UpThreads {
 };
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int RING = 64;  // pending sources per warp (a power of two > 63)
+constexpr int UNIT_STEPS = 3;  // walk steps per loop iteration (unit counts)
 constexpr int NTF = 256;  // threads per finalising block (its walks are few; the loads want warps)
 
 // In-tile offset of direction k (N, NE, E, SE, S, SW, W, NW) for row stride T.
@@ -392,7 +393,12 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(Dem
         } else if (need == FULL) {
           break;
         }
-        if (cur >= 0) {
+        // unit counts: a lane whose walk continues takes a second step in the
+        // same iteration, so the refill and hand-out above are paid once per
+        // two steps of the long walks
+#pragma unroll
+        for (int k = 0; k < (WT ? 1 : UNIT_STEPS); k++) {
+          if (cur < 0) break;
           if (WT) {
             val[cur] = v;
             __threadfence_block();
