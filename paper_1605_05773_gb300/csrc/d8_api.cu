@@ -1,6 +1,8 @@
 // d8_api.cu -- the C ABI of libd8 (declared in include/d8.h): contexts,
 // workspace, argument checks, stage timing, the forward / weighted / backward
 // pipelines and the batch plan with CUDA-graph replay.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -102,7 +104,9 @@ cudaEvent_t get_event(d8_ctx* c) {
   return e;
 }
 
-// RAII bracket of one stage: counts launches, records events when profiling
+// RAII bracket of one stage: an NVTX range named after the stage (host
+// side, around the stage's launches), launch counting, and CUDA events when
+// profiling is on
 struct StageScope {
   d8_ctx* c;
   int st;
@@ -110,12 +114,14 @@ struct StageScope {
   cudaEvent_t a = nullptr;
   int n = 0;
   StageScope(d8_ctx* c_, int st_, cudaStream_t s_) : c(c_), st(st_), s(s_) {
+    nvtxRangePushA(kStageNames[st]);
     if (c->profiling) {
       a = get_event(c);
       cudaEventRecord(a, s);
     }
   }
   ~StageScope() {
+    nvtxRangePop();
     c->launches[st] += n;
     if (c->profiling && a) {
       cudaEvent_t b = get_event(c);

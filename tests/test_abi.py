@@ -46,6 +46,9 @@ def test_host_side_errors_need_no_gpu(lib):
     assert lib.d8_get_status(None, None) == 1
     assert lib.d8_destroy(None) == 0
     assert lib.d8_batch_destroy(None) == 0
+    assert lib.d8_set_strategy(None, 0) == 1
+    assert lib.d8_fill(None, None, 4, 4, 4, ctypes.c_float(1e-3), None, 4, None, None) == 1
+    assert lib.d8_combine_stats(None, None, None, 4) == 1
 
 
 def test_product_does_not_touch_the_oracle():
@@ -56,3 +59,4 @@ def test_product_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "d8_oracle" not in text, f
+                assert "import cpuref" not in text and "d8_cpuref" not in text, f
