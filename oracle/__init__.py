@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "libd8oracle.so")
 _lib = None
 
 OK, ERR_ARG, ERR_NONFINITE, ERR_CYCLE, ERR_NOMEM, ERR_OVERFLOW = 0, 1, 3, 4, 5, 8
-RULES = {"steepest": 0, "lowest": 1}
+RULES = {"steepest": 0, "lowest": 1, "steepest_nodata": 2, "lowest_nodata": 3}
 OUTLET, SINK = 8, 9
 
 

@@ -59,10 +59,16 @@ static float oracle_inv_sqrt2(void) {
 
 /* D8 flow direction of every cell ("The Algorithm": steepest slope with the
  * Euclidean distance between centres; "Introduction": lowest neighbour).
- * rule 0 = steepest, 1 = lowest.  Returns OR_OK, or OR_ERR_NONFINITE if any
- * elevation is NaN or infinite (a non-finite cell itself gets SINK). */
+ * rule bit 0: 0 = steepest, 1 = lowest.  rule bit 1 (NODATA masks): a cell
+ * with a non-finite elevation lies outside the study area and gets OUTLET,
+ * and so does every cell next to one (the area's edge drains off it, as the
+ * grid's edge does).  Returns OR_OK, or (without the NODATA bit)
+ * OR_ERR_NONFINITE if any elevation is NaN or infinite (a non-finite cell
+ * itself gets SINK). */
 int oracle_flowdir(const float* z, int64_t H, int64_t W, int rule, uint8_t* dir) {
-  if (!z || !dir || H < 1 || W < 1 || (rule != 0 && rule != 1)) return OR_ERR_ARG;
+  if (!z || !dir || H < 1 || W < 1 || rule < 0 || rule > 3) return OR_ERR_ARG;
+  const int nodata = rule & 2;
+  rule &= 1;
   const float R = oracle_inv_sqrt2();
   int nonfinite = 0;
   for (int64_t i = 0; i < H; i++) {
@@ -72,6 +78,14 @@ int oracle_flowdir(const float* z, int64_t H, int64_t W, int rule, uint8_t* dir)
       if (i == 0 || j == 0 || i == H - 1 || j == W - 1) {
         dir[i * W + j] = 8; /* OUTLET */
         continue;
+      }
+      if (nodata) {
+        int hole = !isfinite(zc);
+        for (int k = 0; k < 8; k++) hole |= !isfinite(z[(i + ODI[k]) * W + (j + ODJ[k])]);
+        if (hole) {
+          dir[i * W + j] = 8; /* outside the study area, or on its edge */
+          continue;
+        }
       }
       if (!isfinite(zc)) {
         dir[i * W + j] = 9;
@@ -102,7 +116,7 @@ int oracle_flowdir(const float* z, int64_t H, int64_t W, int rule, uint8_t* dir)
       dir[i * W + j] = (uint8_t)best_k;
     }
   }
-  return nonfinite ? OR_ERR_NONFINITE : OR_OK;
+  return (nonfinite && !nodata) ? OR_ERR_NONFINITE : OR_OK;
 }
 
 /* Down-slope neighbour of cell c, or -1 if its path ends at c; -2 for an

@@ -31,6 +31,9 @@ MUTATIONS = {
                          "F[c] = z[c] >= p.f ? z[c] : fill_up(p.f, eps);"),
     # the raise loses its one-step minimum (x + eps can round back to x)
     "fill_no_min_step": ("return a > b ? a : b;", "return a;"),
+    # the NODATA mask forgets the study area's edge (cells next to a hole)
+    "nodata_edge_missed": ("for (int k = 0; k < 8; k++) hole |= !isfinite(z[(i + ODI[k]) * W + (j + ODJ[k])]);",
+                           ""),
     # the flood pops the HIGHEST cell first
     "fill_heap_inverted": ("return a.f < b.f || (a.f == b.f && a.c < b.c);",
                            "return a.f > b.f || (a.f == b.f && a.c < b.c);"),
@@ -45,6 +48,7 @@ PINS = [
     pins.test_weighted_matches_bruteforce_and_linearity,
     pins.test_transposed_adjoint_identity_and_bruteforce,
     pins.test_fill_golden_cases,
+    pins.test_nodata_golden_and_properties,
     pins.test_fill_matches_iteration_on_tiny_grids,
 ]
 

@@ -394,3 +394,43 @@ def test_fill_rejects_nonfinite():
     z[2, 2] = np.nan
     with pytest.raises(oracle.OracleError):
         oracle.fill_eps(z)
+
+
+# ------------------------------------------------------------ NODATA masks
+def test_nodata_golden_and_properties():
+    g = named("nodata_6x6.txt")
+    z = grid(g["z"], np.float32)
+    for rule in ("steepest_nodata", "lowest_nodata"):
+        np.testing.assert_array_equal(oracle.flowdir(z, rule), grid(g[rule], np.uint8), err_msg=rule)
+    # away from holes the mask changes nothing; every hole and every cell next
+    # to one is OUTLET; no error for the non-finite cells
+    rng = np.random.default_rng(20)
+    z = demgen.fractal(120, 97, seed=21, cache=False)
+    holes = rng.random(z.shape) < 0.03
+    z[holes] = np.nan
+    z[40:60, 30:50] = np.nan  # a lake
+    near = holes.copy()
+    near[40:60, 30:50] = True
+    pad = np.pad(near, 1)
+    touch = np.zeros_like(near)
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            touch |= pad[1 + di:1 + di + z.shape[0], 1 + dj:1 + dj + z.shape[1]]
+    for rule in RULES:
+        d = oracle.flowdir(z, rule + "_nodata")
+        assert (d[touch] == 8).all()
+        plain = oracle.flowdir(z, rule, allow_nonfinite=True)
+        np.testing.assert_array_equal(d[~touch], plain[~touch])
+        A = oracle.accumulate(d)  # a valid field: no cycle, conservation holds
+        assert int(A.astype(np.int64)[d >= 8].sum()) + int(
+            A.astype(np.int64)[(d < 8) & _off_grid_targets(d)].sum()) == z.size
+
+
+def _off_grid_targets(d):
+    H, W = d.shape
+    i, j = np.indices(d.shape)
+    DI = np.array([-1, -1, 0, 1, 1, 1, 0, -1])
+    DJ = np.array([0, 1, 1, 1, 0, -1, -1, -1])
+    k = np.minimum(d, 7)
+    ti, tj = i + DI[k], j + DJ[k]
+    return (ti < 0) | (tj < 0) | (ti >= H) | (tj >= W)
