@@ -49,8 +49,13 @@ typedef enum {
 /* Direction rules ("The Algorithm": steepest slope, slope = drop divided by
  * the distance between cell centres, 1 or sqrt 2; "Introduction": lowest
  * neighbour).  Ties go to the first direction in N, NE, E, SE, S, SW, W, NW
- * order; only a strictly positive drop counts. */
-typedef enum { D8_RULE_STEEPEST = 0, D8_RULE_LOWEST = 1 } d8_rule;
+ * order; only a strictly positive drop counts.  D8_RULE_NODATA may be added
+ * to either rule: a cell with a non-finite elevation is then outside the
+ * study area and gets OUTLET, and so does every cell next to one (the area's
+ * edge drains off it, as the grid's edge does), with no error raised.  To
+ * leave such cells out of weighted sums, give them weight 0 (and cell areas
+ * as weights where cells differ in area: "Up-Slope Area"). */
+typedef enum { D8_RULE_STEEPEST = 0, D8_RULE_LOWEST = 1, D8_RULE_NODATA = 2 } d8_rule;
 
 typedef struct d8_ctx d8_ctx;
 typedef struct d8_batch d8_batch;
@@ -85,7 +90,7 @@ d8_status d8_set_strategy(d8_ctx* ctx, int strategy);
 /* D8 flow direction of every cell ("The Algorithm"; "Introduction").
  * z: H x W fp32 elevations (ld ldz); dir: H x W codes (ld lddir).
  * Non-finite z sets D8_ERR_NONFINITE in the status word and gives that cell
- * SINK.  Errors: D8_ERR_ARG. */
+ * SINK, unless the rule carries D8_RULE_NODATA.  Errors: D8_ERR_ARG. */
 d8_status d8_flowdir(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, uint8_t* dir,
                      int64_t lddir, d8_rule rule, d8_stream stream);
 

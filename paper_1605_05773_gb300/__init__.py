@@ -28,7 +28,9 @@ __all__ = [
 ]
 
 OUTLET, SINK = 8, 9
-RULES = {"steepest": 0, "lowest": 1}
+# direction rules; the "_nodata" forms treat non-finite elevations as cells
+# outside the study area (OUTLET, as are the cells next to them)
+RULES = {"steepest": 0, "lowest": 1, "steepest_nodata": 2, "lowest_nodata": 3}
 # in-tile frontier strategies of the unit-count tile passes (identical results)
 STRATEGIES = {"ring": 0, "lane_mask": 1, "jump": 2}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_NONFINITE", 4: "ERR_CYCLE", 5: "ERR_NOMEM",

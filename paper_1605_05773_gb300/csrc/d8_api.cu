@@ -499,7 +499,7 @@ d8_status d8_get_status(d8_ctx* c, d8_stream stream) {
 
 d8_status d8_flowdir(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, uint8_t* dir, int64_t lddir,
                      d8_rule rule, d8_stream stream) {
-  if (!c || bad_grid(z, H, W, ldz) || bad_grid(dir, H, W, lddir) || (rule != 0 && rule != 1)) return D8_ERR_ARG;
+  if (!c || bad_grid(z, H, W, ldz) || bad_grid(dir, H, W, lddir) || (rule < 0 || rule > 3)) return D8_ERR_ARG;
   cudaSetDevice(c->device);
   DemDesc d = make_desc(H, W, c->T);
   d.z = z;
@@ -527,7 +527,7 @@ d8_status d8_accumulate(d8_ctx* c, const uint8_t* dir, int64_t H, int64_t W, int
 d8_status d8_flowdir_accumulate(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
                                 uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA, d8_stream stream) {
   if (!c || bad_grid(z, H, W, ldz) || bad_grid(dir, H, W, lddir) || bad_grid(A, H, W, ldA) ||
-      (rule != 0 && rule != 1))
+      (rule < 0 || rule > 3))
     return D8_ERR_ARG;
   if ((uint64_t)H * (uint64_t)W > 0xFFFFFFFFull) return D8_ERR_SHAPE;
   cudaSetDevice(c->device);
@@ -745,7 +745,7 @@ static cudaError_t batch_enqueue(d8_batch* b, int rule, cudaStream_t s, int* n_u
 
 d8_status d8_batch_flowdir_accumulate(d8_batch* b, const float* const* z, uint8_t* const* dir, uint32_t* const* A,
                                       d8_rule rule, d8_stream stream) {
-  if (!b || !z || !dir || !A || (rule != 0 && rule != 1)) return D8_ERR_ARG;
+  if (!b || !z || !dir || !A || (rule < 0 || rule > 3)) return D8_ERR_ARG;
   d8_ctx* c = b->ctx;
   cudaSetDevice(c->device);
   for (int k = 0; k < b->n; k++) {
@@ -838,7 +838,7 @@ d8_status d8_batch_destroy(d8_batch* b) {
 d8_status d8_batch_autotune(d8_ctx* c, int n, const int64_t* H, const int64_t* W, const float* const* z,
                             uint8_t* const* dir, uint32_t* const* A, d8_rule rule, d8_stream stream, int* best_tile,
                             int* best_strategy, float* ms) {
-  if (!c || !best_tile || n < 1 || !H || !W || !z || !dir || !A || (rule != 0 && rule != 1)) return D8_ERR_ARG;
+  if (!c || !best_tile || n < 1 || !H || !W || !z || !dir || !A || (rule < 0 || rule > 3)) return D8_ERR_ARG;
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   static const int kTiles[3] = {32, 64, 128};

@@ -84,7 +84,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int T>
+// NODATA masks (the rule's NODATA bit): a cell with a non-finite elevation is
+// outside the study area and gets OUTLET, and so does every cell next to one
+// (the area's edge drains off it, as the grid's edge does); nothing is
+// reported as an error.
+template <int T, bool NODATA>
 __global__ void __launch_bounds__(NTF) k_flowdir_rows(DemTable dt, int64_t ntiles, int rule, uint32_t* status) {
   constexpr int CPL = T / 32;  // columns per lane
   constexpr int RW = T + 8;    // floats per buffered row: columns j0 - 4 .. j0 + T + 3
@@ -182,11 +186,14 @@ __global__ void __launch_bounds__(NTF) k_flowdir_rows(DemTable dt, int64_t ntile
         if (redge || coledge[k]) {
           code = 8;
         } else if (!fin) {
-          code = 9;
+          code = NODATA ? 8 : 9;
+        } else if (NODATA && !(isfinite(U[k]) && isfinite(U[k + 1]) && isfinite(U[k + 2]) && isfinite(M[k]) &&
+                               isfinite(M[k + 2]) && isfinite(D[k]) && isfinite(D[k + 1]) && isfinite(D[k + 2]))) {
+          code = 8;
         } else {
           code = window_code(U[k], U[k + 1], U[k + 2], M[k], M[k + 1], M[k + 2], D[k], D[k + 1], D[k + 2], rule);
         }
-        bad |= (k < ncols) && !fin;
+        if (!NODATA) bad |= (k < ncols) && !fin;
         packed |= (uint32_t)code << (8 * k);
       }
       if (bad) set_status(status, D8_ERR_NONFINITE);
@@ -237,15 +244,15 @@ static cudaError_t launch_t(const DemTable& dt, int64_t ntiles, int rule, uint32
   int dev = 0, sms = 1, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flowdir_rows<T>, NTF, 0) != cudaSuccess ||
-      per_sm < 1) {
+  auto k = (rule & 2) ? k_flowdir_rows<T, true> : k_flowdir_rows<T, false>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NTF, 0) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   int64_t grid = (ntiles + WPB - 1) / WPB;
   const int64_t cap = (int64_t)sms * per_sm;
   if (grid > cap) grid = cap;
-  k_flowdir_rows<T><<<(unsigned)(grid < 1 ? 1 : grid), NTF, 0, s>>>(dt, ntiles, rule, status);
+  k<<<(unsigned)(grid < 1 ? 1 : grid), NTF, 0, s>>>(dt, ntiles, rule & 1, status);
   return cudaGetLastError();
 }
 

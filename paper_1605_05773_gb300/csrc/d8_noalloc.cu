@@ -81,7 +81,7 @@ d8_status cuda_rc(cudaError_t e) { return e == cudaSuccess ? D8_OK : D8_ERR_CUDA
 extern "C" d8_status d8_flowdir_accumulate_noalloc(const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
                                                    uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA,
                                                    uint32_t* status, d8_stream stream) {
-  if (!z || !dir || !A || H < 1 || W < 1 || ldz < W || lddir < W || ldA < W || (rule != 0 && rule != 1))
+  if (!z || !dir || !A || H < 1 || W < 1 || ldz < W || lddir < W || ldA < W || (rule < 0 || rule > 3))
     return D8_ERR_ARG;
   if ((uint64_t)H * (uint64_t)W > 0xFFFFFFFFull) return D8_ERR_SHAPE;
   d8::DemDesc d{};

@@ -276,3 +276,22 @@ def test_65536x16384_properties(d8, rule):
     np.testing.assert_array_equal(d.cpu().numpy(), oracle.flowdir(z, rule))
     assert recursion_residual_gpu(d, A) == 0
     assert terminal_sum_gpu(d, A) == H * W
+
+
+@pytest.mark.parametrize("rule", ["steepest_nodata", "lowest_nodata"])
+@pytest.mark.parametrize("shape", [(97, 131), (512, 512), (1500, 1100)])
+def test_nodata_masks(d8, tile, rule, shape):
+    """NODATA masks: non-finite elevations (scattered holes, a lake, a band of
+    NaN and +-inf along a ragged side) are cells outside the study area;
+    directions and counts against the oracle, and no error raised."""
+    H, W = shape
+    z = demgen.fractal(H, W, seed=H + 3 * W, cache=False)
+    rng = np.random.default_rng(H * W)
+    z[rng.random(z.shape) < 0.02] = np.nan
+    z[H // 3:H // 2, W // 4:W // 3] = np.nan
+    z[:, W - 5:W - 2] = np.inf
+    z[H - 7, :W // 2] = -np.inf
+    d, A = _fused(d8, z, rule)
+    d_ref = oracle.flowdir(z, rule)
+    np.testing.assert_array_equal(d, d_ref)
+    np.testing.assert_array_equal(A, oracle.accumulate(d_ref))
