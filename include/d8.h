@@ -114,6 +114,28 @@ d8_status d8_accumulate(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, i
 d8_status d8_flowdir_accumulate(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,
                                 uint8_t* dir, int64_t lddir, uint32_t* A, int64_t ldA, d8_stream stream);
 
+/* Directions of a horizontal strip of a taller grid (the paper's row-strip
+ * partition, "The Algorithm": each partition owns consecutive rows and sees
+ * one row of its neighbours).  As d8_flowdir on the H x W strip, except that
+ * halo bit 0 says the row above the strip's first row is readable at
+ * z - ldz and belongs to the grid (the first row is then not an edge and gets
+ * a real direction, possibly towards that row), and bit 1 the same for the
+ * row below the last row (at z + H*ldz).  Codes pointing out of the strip end
+ * a path when the strip's directions are accumulated on their own: those
+ * cells are the strip's exits.  Errors: D8_ERR_ARG. */
+d8_status d8_flowdir_strip(d8_ctx* ctx, const float* z, int64_t H, int64_t W, int64_t ldz, int halo, d8_rule rule,
+                           uint8_t* dir, int64_t lddir, d8_stream stream);
+
+/* Unit up-slope counts of a direction field that also receives flow from
+ * outside across its first and last rows (Algorithms 7-8 for a strip whose
+ * neighbours' resolved exits drain into it): A(p) = 1 + sum of A over the
+ * cells draining into p + in(p), where in(0, j) = top_in[j] and
+ * in(H-1, j) = bottom_in[j] (device arrays of W uint32; either may be NULL
+ * for none).  Otherwise as d8_accumulate. */
+d8_status d8_accumulate_inflow(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
+                               const uint32_t* top_in, const uint32_t* bottom_in, uint32_t* A, int64_t ldA,
+                               d8_stream stream);
+
 /* Weighted up-slope area A(p) = w(p) + sum of A over the cells draining into
  * p (Eq. 1 with the paragraph after it: cells "may or may not be weighted
  * equally").  fp32 in and out, compensated (TwoSum) fp32 accumulation

@@ -22,7 +22,7 @@ import torch
 from . import build as _build
 
 __all__ = [
-    "load", "fill", "flowdir", "accumulate", "set_strategy", "STRATEGIES", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
+    "load", "fill", "flowdir", "flowdir_strip", "accumulate", "accumulate_inflow", "set_strategy", "STRATEGIES", "flowdir_accumulate", "accumulate_weighted", "accumulate_backward",
     "weighted_upslope", "WeightedUpslope", "BatchPlan", "autotune_batch", "shape_class", "get_status", "set_tile", "set_profiling",
     "stage_times", "combine_stats", "D8Error", "OUTLET", "SINK", "RULES",
 ]
@@ -79,6 +79,8 @@ def load() -> ctypes.CDLL:
             "d8_flowdir": [vp, vp, i64, i64, i64, vp, i64, i32, vp],
             "d8_accumulate": [vp, vp, i64, i64, i64, vp, i64, vp],
             "d8_flowdir_accumulate": [vp, vp, i64, i64, i64, i32, vp, i64, vp, i64, vp],
+            "d8_flowdir_strip": [vp, vp, i64, i64, i64, i32, i32, vp, i64, vp],
+            "d8_accumulate_inflow": [vp, vp, i64, i64, i64, vp, vp, vp, i64, vp],
             "d8_accumulate_weighted": [vp, vp, i64, i64, i64, vp, i64, vp, i64, vp],
             "d8_accumulate_backward": [vp, vp, i64, i64, i64, vp, i64, vp, i64, vp],
             "d8_batch_plan": [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp)],
@@ -212,6 +214,42 @@ def accumulate(dir: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tens
     _same_shape(dir, A, "dir/out")
     _check(load().d8_accumulate(context(dir.device), dir.data_ptr(), H, W, ldd, A.data_ptr(), lda, _stream(dir)),
            "d8_accumulate")
+    return A
+
+
+def flowdir_strip(z: torch.Tensor, halo: int, rule: str = "steepest", out: torch.Tensor | None = None) -> torch.Tensor:
+    """Directions of a horizontal strip of a taller grid (d8_flowdir_strip).
+    z: a view of the strip's rows inside a larger row-major tensor; halo bit 0
+    means the row above the view belongs to the grid (and is readable), bit 1
+    the row below."""
+    H, W, ldz = _grid(z, torch.float32, "z")
+    d = torch.empty((H, W), dtype=torch.uint8, device=z.device) if out is None else out
+    _, _, ldd = _grid(d, torch.uint8, "out")
+    _same_shape(z, d, "z/out")
+    _check(load().d8_flowdir_strip(context(z.device), z.data_ptr(), H, W, ldz, int(halo), RULES[rule], d.data_ptr(),
+                                   ldd, _stream(z)), "d8_flowdir_strip")
+    return d
+
+
+def accumulate_inflow(dir: torch.Tensor, top_in: torch.Tensor | None, bottom_in: torch.Tensor | None,
+                      out: torch.Tensor | None = None) -> torch.Tensor:
+    """Unit counts with flow entering across the first and last rows
+    (d8_accumulate_inflow): top_in[j] enters cell (0, j), bottom_in[j] cell
+    (H-1, j); uint32 CUDA vectors of length W, or None."""
+    H, W, ldd = _grid(dir, torch.uint8, "dir")
+    A = torch.empty((H, W), dtype=torch.uint32, device=dir.device) if out is None else out
+    _, _, lda = _grid(A, torch.uint32, "out")
+    _same_shape(dir, A, "dir/out")
+    ptrs = []
+    for t, nm in ((top_in, "top_in"), (bottom_in, "bottom_in")):
+        if t is None:
+            ptrs.append(None)
+            continue
+        if not t.is_cuda or t.dtype != torch.uint32 or t.dim() != 1 or t.shape[0] != W or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous CUDA uint32 vector of length {W}")
+        ptrs.append(t.data_ptr())
+    _check(load().d8_accumulate_inflow(context(dir.device), dir.data_ptr(), H, W, ldd, ptrs[0], ptrs[1],
+                                       A.data_ptr(), lda, _stream(dir)), "d8_accumulate_inflow")
     return A
 
 

@@ -300,7 +300,8 @@ bool slots_fit(int64_t ntiles, int T) { return (uint64_t)ntiles * 4 * (uint64_t)
 
 // forward pipeline on one DEM: directions (when z is given), tile pass,
 // combine, finalise
-d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStream_t s) {
+d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStream_t s,
+                      const uint32_t* top_in = nullptr, const uint32_t* bot_in = nullptr) {
   const int T = c->T;
   DemDesc d = d0;
   const int64_t ntiles = d.ntx * d.nty;
@@ -315,6 +316,8 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   if (st != D8_OK) return st;
   Pipe p = carve_pipe(c->ws, ntiles, T, vb, c->status);
   p.strat = c->strat;
+  p.top_in = top_in;
+  p.bot_in = bot_in;
   DemTable dt = single(d);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -327,6 +330,7 @@ d8_status run_forward(d8_ctx* c, const DemDesc& d0, int mode, int rule, cudaStre
   {
     StageScope sc(c, ST_UP, s);
     e = launch_up(dt, p, mode, rule, s, &sc.n);
+    if (e == cudaSuccess && (top_in || bot_in)) e = launch_inject_inflow(d, p, s, &sc.n);
   }
   if (e != cudaSuccess) return cuda_fail(e);
   {
@@ -522,6 +526,36 @@ d8_status d8_accumulate(d8_ctx* c, const uint8_t* dir, int64_t H, int64_t W, int
   d.A = A;
   d.ldA = ldA;
   return run_forward(c, d, UP_UNIT_DIR, 0, static_cast<cudaStream_t>(stream));
+}
+
+d8_status d8_flowdir_strip(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, int halo, d8_rule rule,
+                           uint8_t* dir, int64_t lddir, d8_stream stream) {
+  if (!c || bad_grid(z, H, W, ldz) || bad_grid(dir, H, W, lddir) || (rule < 0 || rule > 3) || halo < 0 || halo > 3)
+    return D8_ERR_ARG;
+  cudaSetDevice(c->device);
+  DemDesc d = make_desc(H, W, c->T);
+  d.z = z;
+  d.ldz = ldz;
+  d.dir = dir;
+  d.lddir = lddir;
+  d.halo = halo;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StageScope sc(c, ST_FLOWDIR, s);
+  return cuda_fail(launch_flowdir(single(d), d.ntx * d.nty, c->T, (int)rule, c->status, s, &sc.n));
+}
+
+d8_status d8_accumulate_inflow(d8_ctx* c, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
+                               const uint32_t* top_in, const uint32_t* bottom_in, uint32_t* A, int64_t ldA,
+                               d8_stream stream) {
+  if (!c || bad_grid(dir, H, W, lddir) || bad_grid(A, H, W, ldA)) return D8_ERR_ARG;
+  if ((uint64_t)H * (uint64_t)W > 0xFFFFFFFFull) return D8_ERR_SHAPE;
+  cudaSetDevice(c->device);
+  DemDesc d = make_desc(H, W, c->T);
+  d.dir = const_cast<uint8_t*>(dir);
+  d.lddir = lddir;
+  d.A = A;
+  d.ldA = ldA;
+  return run_forward(c, d, UP_UNIT_DIR, 0, static_cast<cudaStream_t>(stream), top_in, bottom_in);
 }
 
 d8_status d8_flowdir_accumulate(d8_ctx* c, const float* z, int64_t H, int64_t W, int64_t ldz, d8_rule rule,

@@ -117,8 +117,10 @@ __global__ void __launch_bounds__(NTF) k_flowdir_rows(DemTable dt, int64_t ntile
     // rows q in [qlo, qhi) lie on the grid (the others only neighbour edge
     // cells, whose code is OUTLET, and are never fetched); row q + PD is
     // fetched while row q is used, from a pointer advanced by ldz per row
-    const int qlo = g.i0 == 0 ? 1 : 0;
-    const int qhi = (int)min64((int64_t)nq, d.H - g.i0 + 1);
+    // (a strip of a taller grid also reads the row above its first row or
+    // below its last, d.halo, whose cells are then not grid edges)
+    const int qlo = (g.i0 == 0 && !(d.halo & 1)) ? 1 : 0;
+    const int qhi = (int)min64((int64_t)nq, d.H - g.i0 + ((d.halo & 2) ? 2 : 1));
     // fetch() is called for q = 0, 1, 2, ... in order: a running row pointer
     const float* fsrc = d.z + (g.i0 - 1) * d.ldz + col0;  // row q = 0; only formed, not read, when i0 == 0
     int fq = 0;
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(NTF) k_flowdir_rows(DemTable dt, int64_t ntile
       Wr[0] = lane == 0 ? row[-1] : ls;
       Wr[CPL + 1] = lane == 31 ? row[CPL] : rs;
     };
-    const int i_top_edge = (g.i0 == 0) ? 0 : -10;
-    const int i_bot_edge = (g.i0 + g.th == d.H) ? g.th - 1 : -10;
+    const int i_top_edge = (g.i0 == 0 && !(d.halo & 1)) ? 0 : -10;
+    const int i_bot_edge = (g.i0 + g.th == d.H && !(d.halo & 2)) ? g.th - 1 : -10;
     const int ncols = max(0, min(CPL, g.tw - jb));  // own columns present
     uint8_t* drow = d.dir + g.i0 * d.lddir + g.j0 + jb;  // emit() is called for rows 0, 1, 2, ... in order
     const bool st_vec = (ncols == CPL) && ((reinterpret_cast<uintptr_t>(drow) & (CPL - 1)) == 0) &&

@@ -92,6 +92,32 @@ __global__ void k_pj_check(Pipe p, int R) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && p.flags[R] != 0u) set_status(p.status, D8_ERR_CYCLE);
 }
 
+// Inflow entering the grid across its first and last rows (a strip of a
+// taller grid receiving from its neighbours): the flow entering cell (0, j)
+// or (H-1, j) follows that cell's in-tile path, so it is added to the value of
+// the tile exit the path reaches (Algorithm 7's receivers, seen from the
+// combine), or to nothing when the path ends in the tile.  The finalising pass
+// then adds it along the path itself.
+template <int T>
+__global__ void k_inject_inflow(DemDesc d, Pipe p) {
+  uint32_t* pval = static_cast<uint32_t*>(p.pval);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * d.W; q += stride) {
+    const bool bottom = q >= d.W;
+    const int64_t j = bottom ? q - d.W : q, gi = bottom ? d.H - 1 : 0;
+    const uint32_t* in = bottom ? p.bot_in : p.top_in;
+    if (!in) continue;
+    const uint32_t v = in[j];
+    if (!v) continue;
+    const int64_t ty = gi / T, tx = j / T, t = ty * d.ntx + tx;
+    const int th = (int)min64(T, d.H - ty * T), tw = (int)min64(T, d.W - tx * T);
+    const int s = slot_of((int)(gi - ty * T), (int)(j - tx * T), th, tw, T);
+    const uint16_t pe = p.pex[t * (4 * T) + s];
+    const int e = (pe & PEX_EXIT) ? s : (pe == PEX_TERM ? -1 : (int)pe);
+    if (e >= 0) atomicAdd(&pval[t * (4 * T) + e], v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host launchers
 
@@ -161,6 +187,18 @@ cudaError_t launch_combine_flat(const DemTable& dt, const Pipe& p, cudaStream_t 
     case 128: return launch_combine_fwd_t<128, uint32_t>(dt, p, s, nlaunch);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_inject_inflow(const DemDesc& d, const Pipe& p, cudaStream_t s, int* nlaunch) {
+  const unsigned g = grid_for(2 * d.W);
+  ++*nlaunch;
+  switch (p.T) {
+    case 32: k_inject_inflow<32><<<g, 256, 0, s>>>(d, p); break;
+    case 64: k_inject_inflow<64><<<g, 256, 0, s>>>(d, p); break;
+    case 128: k_inject_inflow<128><<<g, 256, 0, s>>>(d, p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_down(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch) {

@@ -24,6 +24,9 @@ struct DemDesc {
   int64_t H, W;
   int64_t ntx, nty;
   int64_t tile_base;  // global index of this DEM's first tile
+  int halo;           // direction stencil: bit 0 the row above row 0 is readable (z - ldz) and row 0
+                      // is not a grid edge; bit 1 the same for the row below row H-1 (a strip of a
+                      // taller grid)
 };
 
 // The DEMs of a launch: either one descriptor passed by value, or a device
@@ -63,6 +66,8 @@ struct Pipe {
   uint32_t* status;  // device status word (OR of 1 << d8_status)
   uint32_t* queue;   // tile work-queue counters (one per stage)
   uint16_t* xid;     // adjoint only: per cell (row-major, W per row) the slot of its tile exit, or NO_EXIT
+  const uint32_t* top_in;  // unit counts: inflow entering row 0 from above, per column (or null)
+  const uint32_t* bot_in;  // unit counts: inflow entering row H-1 from below, per column (or null)
 };
 constexpr uint16_t NO_EXIT = 0xFFFFu;
 
@@ -75,6 +80,10 @@ cudaError_t launch_up(const DemTable& dt, const Pipe& p, int mode, int rule, cud
 // flat pointer-jumping combine of unit counts (the allocation-free entry point)
 cudaError_t launch_combine_flat(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_down(const DemTable& dt, const Pipe& p, bool weighted, cudaStream_t s, int* nlaunch);
+// unit counts, one DEM: the inflow entering across its top and bottom rows
+// (p.top_in, p.bot_in) added to the tile summaries' exit values before the
+// combine
+cudaError_t launch_inject_inflow(const DemDesc& d, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_bwd_up(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_combine_bwd(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);
 cudaError_t launch_bwd_down(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch);

@@ -644,6 +644,15 @@ __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
         in += xval[global_slot(d, gi, gj, T)];
         any = true;
       }
+      // flow entering across the grid's first or last row (a strip)
+      if (p.top_in && g.i0 + i == 0 && p.top_in[g.j0 + j]) {
+        in += p.top_in[g.j0 + j];
+        any = true;
+      }
+      if (p.bot_in && g.i0 + i == d.H - 1 && p.bot_in[g.j0 + j]) {
+        in += p.bot_in[g.j0 + j];
+        any = true;
+      }
       if (any) {
         const int r = atomicAdd(&misc[0], 1);
         rcell[r] = (uint16_t)(i * T + j);
