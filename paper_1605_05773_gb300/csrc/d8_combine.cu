@@ -19,6 +19,8 @@
 //
 // Unit counts travel as uint32, weighted areas as float-float values (fp32
 // arithmetic throughout, with compensated atomic adds).
+#include <cstring>
+
 #include "d8_device.cuh"
 
 namespace d8 {
@@ -93,23 +95,48 @@ template <int S, int G, class V, class CV>
 __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint16_t* cpex, const CV* cpval,
                           uint16_t* spx, V* val, uint32_t* pd) {
   constexpr int NS = G * G * 4 * S;
+  constexpr int SPT = 4 * S;  // slots per child, a multiple of 8
+  constexpr int NQ = NS / 8 / NTG > 0 ? NS / 8 / NTG : 1;
+  static_assert(SPT % 8 == 0 && NS % (8 * NTG) == 0, "eight slots per load, whole rounds per thread");
   int exits = 0;
-  for (int n = threadIdx.x; n < NS; n += NTG) {
-    const int lt = n / (4 * S), s = n - lt * (4 * S);
+  // eight consecutive slots of one child per 16-byte load of codes, with
+  // their values loaded unconditionally beside them: every load of this
+  // thread is issued before any is used (one round trip to memory)
+  uint4 pe8[NQ];
+  CV v8[NQ][8];
+#pragma unroll
+  for (int r = 0; r < NQ; r++) {
+    const int n = (threadIdx.x + r * NTG) * 8;
+    const int lt = n / SPT, s = n - lt * SPT;
     const int64_t cy = gy * G + lt / G, cx = gx * G + lt % G;
-    uint16_t pe = PEX_TERM;
-    V v{};
+    pe8[r] = make_uint4(PEX_TERM | (PEX_TERM << 16), PEX_TERM | (PEX_TERM << 16), PEX_TERM | (PEX_TERM << 16),
+                        PEX_TERM | (PEX_TERM << 16));
     if (cy < cd.nty && cx < cd.ntx) {
-      const int64_t cu = cd.tile_base + cy * cd.ntx + cx;
-      pe = cpex[cu * (4 * S) + s];
-      if (pe & PEX_EXIT) {
-        v = cpval[cu * (4 * S) + s];
-        exits++;
-      }
+      const int64_t g0 = (cd.tile_base + cy * cd.ntx + cx) * SPT + s;
+      pe8[r] = *reinterpret_cast<const uint4*>(cpex + g0);
+      const uint4* vp = reinterpret_cast<const uint4*>(cpval + g0);
+      uint4 raw[8 * sizeof(CV) / 16];
+#pragma unroll
+      for (int k = 0; k < (int)(8 * sizeof(CV) / 16); k++) raw[k] = vp[k];
+      memcpy(v8[r], raw, sizeof(raw));
     }
-    spx[n] = pe;
-    val[n] = v;
-    pd[n] = 0;
+  }
+#pragma unroll
+  for (int r = 0; r < NQ; r++) {
+    const int n = (threadIdx.x + r * NTG) * 8;
+    const uint16_t* pe = reinterpret_cast<const uint16_t*>(&pe8[r]);
+    V vo[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const bool ex = (pe[k] & PEX_EXIT) != 0;
+      exits += ex;
+      vo[k] = ex ? V(v8[r][k]) : V{};
+    }
+    *reinterpret_cast<uint4*>(spx + n) = pe8[r];
+#pragma unroll
+    for (int k = 0; k < 8; k++) val[n + k] = vo[k];
+    *reinterpret_cast<uint4*>(pd + n) = make_uint4(0, 0, 0, 0);
+    *reinterpret_cast<uint4*>(pd + n + 4) = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
   for (int n = threadIdx.x; n < NS; n += NTG) {
