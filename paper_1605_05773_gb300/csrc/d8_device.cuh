@@ -62,6 +62,25 @@ struct VOps<uint32_t> {
 };
 
 
+// ---- asynchronous global -> shared copies (bytes in flight cost no registers)
+// nbytes < copy size zero-fills the rest; a 16-byte copy needs both addresses
+// 16-byte aligned, a 4-byte copy 4-byte aligned
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(nbytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int nbytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(nbytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // DEM of a tile, by value so its fields can live in registers
 __device__ __forceinline__ DemDesc dem_of(const DemTable& t, int64_t tile) {
   if (t.ndem == 1) return t.one;

@@ -68,21 +68,6 @@ __device__ __forceinline__ int window_code(float a0, float a1, float a2, float b
   return code;
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int nbytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(nbytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, int nbytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(nbytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // NODATA masks (the rule's NODATA bit): a cell with a non-finite elevation is
 // outside the study area and gets OUTLET, and so does every cell next to one

@@ -154,11 +154,12 @@ struct UpLayout {
 template <int T>
 struct FinLayout {
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t off_f = 0;                     // uint32 F per cell
+  static constexpr size_t off_f = 0;                     // uint32 per cell: A + inflow
   static constexpr size_t off_code = TT * 4;             // uint8 code per cell
   static constexpr size_t off_rcell = off_code + TT;     // uint16 per perimeter slot
   static constexpr size_t off_rin = off_rcell + (size_t)4 * T * 2;  // uint32 per slot
-  static constexpr size_t off_misc = off_rin + (size_t)4 * T * 4;
+  static constexpr size_t off_ring = off_rin + (size_t)4 * T * 4;   // uint8 codes around the tile
+  static constexpr size_t off_misc = (off_ring + 2 * (T + 2) + 2 * T + 15) / 16 * 16;
   static constexpr size_t bytes = off_misc + 64;
 };
 
@@ -577,9 +578,9 @@ __global__ void __launch_bounds__(NTU, 8) k_up_lm(DemTable dt, Pipe p) {
   }
 }
 
-// Algorithms 7-8 restricted to where they change anything.  A already holds
-// the in-tile counts; the final count is A(c) + F(c), where F(c) is the
-// inflow from other tiles routed through c.  Inflow enters a tile only at its
+// Algorithms 7-8 restricted to where they change anything.  The final count
+// is A(c) + F(c), where A holds the in-tile counts and F(c) is the inflow
+// from other tiles routed through c.  Inflow enters a tile only at its
 // receivers (perimeter cells with an up-slope neighbour in another tile) and
 // follows the unique down-slope path from there, so F(c) is the sum of the
 // receivers' inflows over the receivers whose in-tile path passes through c.
@@ -589,46 +590,86 @@ __global__ void __launch_bounds__(NTU, 8) k_up_lm(DemTable dt, Pipe p) {
 // receiver (about a sixth of a 64 x 64 tile on fractal terrain) are touched.
 // The work is the summed length of the receivers' in-tile paths (at most
 // 4T * T^2 for adversarial fields, about the sub-forest size on terrain).
+//
+// Memory: the tile's codes and the codes of the one-cell ring around it are
+// requested together (asynchronous copies into shared memory), so a tile
+// costs one round trip for them, one for the receivers' resolved inflows and
+// a read-modify-write of the 16-byte quads of A where the inflow is non-zero.  (Reading
+// the tile's whole A up front instead, into the array the walks add to, was
+// slower: the sparse read-modify-write moves fewer bytes.)
 template <int T>
 __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
   using L = FinLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
-  uint32_t* F = reinterpret_cast<uint32_t*>(sm + L::off_f);
+  uint32_t* F = reinterpret_cast<uint32_t*>(sm + L::off_f);  // inflow through each cell
   uint8_t* code = sm + L::off_code;
   uint16_t* rcell = reinterpret_cast<uint16_t*>(sm + L::off_rcell);
   uint32_t* rin = reinterpret_cast<uint32_t*>(sm + L::off_rin);
+  uint8_t* ring = sm + L::off_ring;        // codes around the tile: top T+2, bottom T+2, left T, right T
   int* misc = reinterpret_cast<int*>(sm + L::off_misc);
   const uint32_t* xval = static_cast<const uint32_t*>(p.S);
   constexpr int TT = T * T;
+  constexpr int NQ = TT / 4 / NTF > 0 ? TT / 4 / NTF : 1;  // quads per thread in the write-back
 
-  // F[] starts at zero; every tile leaves it at zero again (the output pass
-  // clears the words the walks touched)
-  for (int c = threadIdx.x; c < TT / 4; c += NTF) reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
-  if (threadIdx.x == 0) misc[0] = 0;
-
+  // F starts at zero; every tile leaves the words it touched at zero again
+  for (int q = threadIdx.x; q < TT / 4; q += NTF) reinterpret_cast<uint4*>(F)[q] = make_uint4(0, 0, 0, 0);
   TileQueue tq(p.queue + 1, p.ntiles);
   for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
-    // the tile's codes (cells outside a ragged tile are never reached)
+    if (threadIdx.x == 0) misc[0] = 0;
+    // the tile's codes copied straight into shared memory, and the codes of
+    // the ring around it, all requested before any is waited for
     {
-      const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
-      for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-        const int c = q * 4, i = c / T, j = c - i * T;
-        if (i >= g.th) continue;
-        const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
-        uint32_t four = 0x08080808u;
-        if (vec) {
-          four = __ldg(reinterpret_cast<const unsigned int*>(src));
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (j + k < g.tw) four = (four & ~(0xFFu << (8 * k))) | ((uint32_t)src[k] << (8 * k));
+      const bool vecD = g.tw == T && ((reinterpret_cast<uintptr_t>(d.dir) & 15u) == 0) && (d.lddir % 16 == 0);
+      for (int q = threadIdx.x; q < TT / 16; q += NTF) {  // 16 codes at a time
+        const int c = q * 16, i = c / T, j = c - i * T;
+        uint8_t* dst = code + c;
+        if (i >= g.th) {
+          *reinterpret_cast<uint4*>(dst) = make_uint4(0x08080808u, 0x08080808u, 0x08080808u, 0x08080808u);
+          continue;
         }
-        reinterpret_cast<uint32_t*>(code)[q] = four;
+        const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
+        if (vecD) {
+          cp_async16(dst, src, 16);
+        } else {
+#pragma unroll 4
+          for (int k = 0; k < 16; k++) dst[k] = j + k < g.tw ? src[k] : (uint8_t)8;
+        }
       }
+      cp_async_commit();
+      // the ring of codes around the tile (0xFF off the grid)
+      for (int q = threadIdx.x; q < 2 * (T + 2) + 2 * T; q += NTF) {
+        int li, lj;
+        if (q < T + 2) {
+          li = -1;
+          lj = q - 1;
+        } else if (q < 2 * (T + 2)) {
+          li = g.th;
+          lj = q - (T + 2) - 1;
+        } else if (q < 2 * (T + 2) + T) {
+          li = q - 2 * (T + 2);
+          lj = -1;
+        } else {
+          li = q - 2 * (T + 2) - T;
+          lj = g.tw;
+        }
+        const int64_t gi = g.i0 + li, gj = g.j0 + lj;
+        uint8_t v = 0xFF;
+        if (gi >= 0 && gj >= 0 && gi < d.H && gj < d.W && li <= g.th && lj <= g.tw && (q < 2 * (T + 2) || li < g.th))
+          v = d.dir[gi * d.lddir + gj];
+        ring[q] = v;
+      }
+      cp_async_wait<0>();
     }
+    __syncthreads();
     // Algorithm 7: the receivers and their resolved inflow, listed
+    auto ring_code = [&](int li, int lj) -> uint32_t {  // code of a cell just outside the tile
+      if (li < 0) return ring[lj + 1];
+      if (li >= g.th) return ring[(T + 2) + lj + 1];
+      if (lj < 0) return ring[2 * (T + 2) + li];
+      return ring[2 * (T + 2) + T + li];
+    };
     for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
@@ -638,10 +679,8 @@ __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
       for (int k = 0; k < 8; k++) {
         const int li = i + code_di(k), lj = j + code_dj(k);
         if (li >= 0 && lj >= 0 && li < g.th && lj < g.tw) continue;
-        const int64_t gi = g.i0 + li, gj = g.j0 + lj;
-        if (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) continue;
-        if (d.dir[gi * d.lddir + gj] != opposite(k)) continue;
-        in += xval[global_slot(d, gi, gj, T)];
+        if (ring_code(li, lj) != (uint32_t)opposite(k)) continue;  // also rejects cells off the grid
+        in += xval[global_slot(d, g.i0 + li, g.j0 + lj, T)];
         any = true;
       }
       // flow entering across the grid's first or last row (a strip)
@@ -679,9 +718,10 @@ __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) misc[0] = 0;
-    // A += F where F is nonzero; touched words go back to zero
-    for (int q = threadIdx.x; q < TT / 4; q += NTF) {
+    // A += F where F is non-zero; those F words go back to zero
+#pragma unroll
+    for (int r = 0; r < NQ; r++) {
+      const int q = threadIdx.x + r * NTF;
       const uint4 f = reinterpret_cast<const uint4*>(F)[q];
       if (!(f.x | f.y | f.z | f.w)) continue;
       reinterpret_cast<uint4*>(F)[q] = make_uint4(0, 0, 0, 0);
