@@ -148,9 +148,10 @@ d8_status d8_accumulate_weighted(d8_ctx* ctx, const uint8_t* dir, int64_t H, int
  * dw(q) = dL/dw(q) = dA(q) + dw(down-slope neighbour of q), i.e. the sum of
  * dA over q's flow path (the transpose of Eq. 1).  Per-tile path sums, a
  * pointer-jumping solve over the tile exits, then a finalising pass; the
- * tiles are 32 x 32 whatever d8_set_tile says (their shared-memory need per
- * cell makes larger tiles slower).  fp32 in and out, compensated
- * accumulation.  Errors as d8_accumulate. */
+ * tiles are 64 x 64, or 32 x 32 when d8_set_tile chose 32 (128 x 128 tiles
+ * would not fit in shared memory).  Deterministic: the result does not depend
+ * on the launch configuration.  fp32 in and out, compensated accumulation.
+ * Errors as d8_accumulate. */
 d8_status d8_accumulate_backward(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
                                  const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream);
 

@@ -593,10 +593,10 @@ d8_status d8_accumulate_backward(d8_ctx* c, const uint8_t* dir, int64_t H, int64
                                  const float* dA, int64_t lddA, float* dw, int64_t lddw, d8_stream stream) {
   if (!c || bad_grid(dir, H, W, lddir) || bad_grid(dA, H, W, lddA) || bad_grid(dw, H, W, lddw)) return D8_ERR_ARG;
   cudaSetDevice(c->device);
-  // The adjoint's tile passes double-buffer their pointer-jumping arrays (about
-  // 25 bytes of shared memory per cell), so they use 32 x 32 tiles whatever the
-  // context's tile side: larger tiles would leave too few tiles per SM.
-  const int T = 32;
+  // The adjoint's tile pass keeps 21 bytes of shared memory per cell, so 64 x 64
+  // tiles fit two per SM; a context set to 32 x 32 tiles uses those (128 x 128
+  // would not fit).
+  const int T = c->T == 32 ? 32 : 64;
   DemDesc d = make_desc(H, W, T);
   d.dir = const_cast<uint8_t*>(dir);
   d.lddir = lddir;
@@ -606,12 +606,17 @@ d8_status d8_accumulate_backward(d8_ctx* c, const uint8_t* dir, int64_t H, int64
   d.ldA = lddw;
   const int64_t ntiles = d.ntx * d.nty;
   if (!slots_fit(ntiles, T)) return D8_ERR_SHAPE;
-  // the pipe, then one uint16 per cell: the slot of the cell's tile exit
+  // the pipe, one uint16 per cell (the slot of the cell's tile exit) and two
+  // lists of slots for the combine's rounds
   const size_t pb = align256(pipe_bytes(ntiles, T, 8));
-  d8_status st = ensure_ws(c, pb + align256((size_t)H * (size_t)W * 2));
+  const size_t xb = align256((size_t)H * (size_t)W * 2);
+  const size_t lb = align256((size_t)ntiles * 4 * T * 4);
+  d8_status st = ensure_ws(c, pb + xb + 2 * lb);
   if (st != D8_OK) return st;
   Pipe p = carve_pipe(c->ws, ntiles, T, 8, c->status);
   p.xid = reinterpret_cast<uint16_t*>(static_cast<char*>(c->ws) + pb);
+  p.list[0] = reinterpret_cast<uint32_t*>(static_cast<char*>(c->ws) + pb + xb);
+  p.list[1] = reinterpret_cast<uint32_t*>(static_cast<char*>(c->ws) + pb + xb + lb);
   DemTable dt = single(d);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(uint32_t) * 16, s);

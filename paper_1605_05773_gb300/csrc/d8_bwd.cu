@@ -4,207 +4,282 @@
 //   dw(q) = dL/dw(q) = dA(q) + dw(down-slope neighbour of q)   (0 past a path end),
 // i.e. the sum of dA along q's flow path.  Same partition scheme as forward:
 //  k_bwd_up    per tile: path sums to the tile exit for every cell by pointer
-//              jumping in shared memory; the perimeter summary records, per
-//              perimeter cell, its exit slot and its in-tile path sum.
+//              jumping; the perimeter summary records, per perimeter cell,
+//              its exit slot and its in-tile path sum.  It also writes every
+//              cell's in-tile path sum to dw and the slot of its tile exit to
+//              a per-cell array.
 //  k_bpj_*     combine: for each exit x with successor y in the next tile,
 //              H(x) = (path sum of y inside its tile) + H(exit of y); a path
 //              sum over the exit forest, found by pointer jumping (gathers
-//              only, so deterministic).
-//              It also writes every cell's in-tile path sum to dw and the
-//              slot of its tile exit to a per-cell array.
+//              only, so deterministic) over a list of the exits whose sums
+//              are still open.
 //  k_bwd_fix   streaming: dw(q) += H(exit of q) for the cells whose path
 //              leaves their tile (float-float add of the rounded path sum).
+//
+// Both pointer-jumping stages are synchronous (Jacobi) rounds, so every sum is
+// formed in the same order whatever the schedule: the result does not depend
+// on the launch configuration.  Work per round is proportional to the cells
+// or exits whose sums are still open, not to the tile or slot count.
 #include "d8_device.cuh"
 
 namespace d8 {
 
-constexpr uint16_t NX_END = 0xFFFFu;
+// nx entry of a cell whose in-tile path sum is complete; the low bits hold the
+// last cell of its in-tile path (a tile exit or a path end)
+constexpr uint16_t NX_DONE = 0x8000u;
+
+// 64 x 64 tiles take 512 threads (8 cells each), 32 x 32 tiles 256 (4 each)
+template <int T>
+struct BwdCfg {
+  static constexpr int NTB = T >= 64 ? 512 : 256;
+  static constexpr int CPT = T * T / NTB;
+  static constexpr int MAXR = T >= 64 ? 13 : 11;  // > log2 of the longest in-tile path (T*T cells)
+};
 
 template <int T>
 struct BwdLayout {
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t off_gs = 0;                          // ff [2][TT]
-  static constexpr size_t off_nx = off_gs + 2 * TT * sizeof(ff);  // u16 [2][TT]
-  static constexpr size_t off_en = off_nx + 2 * TT * 2;         // u16 [2][TT]
-  static constexpr size_t off_cl = off_en + 2 * TT * 2;         // u8 [TT]
-  static constexpr size_t off_misc = off_cl + (TT + 15) / 16 * 16;
-  static constexpr size_t bytes = off_misc + 16;
+  static constexpr size_t off_gs = 0;                      // ff [2][TT]: path sum over the cells included so far
+  static constexpr size_t off_nx = 2 * TT * sizeof(ff);    // u16 [2][TT]: next cell not yet included, or NX_DONE | last
+  static constexpr size_t off_cl = off_nx + 2 * TT * 2;    // u8 [TT]: class of the cell
+  static constexpr size_t bytes = off_cl + TT;
 };
 
-size_t bwd_smem_bytes(int T) {
-  size_t b = 0;
-  switch (T) {
-    case 32: b = BwdLayout<32>::bytes; break;
-    case 64: b = BwdLayout<64>::bytes; break;
-    case 128: b = BwdLayout<128>::bytes; break;
-    default: return 0;
-  }
-  return b <= 227 * 1024 ? b : 0;
-}
-
-// In-tile path sums by synchronous pointer jumping: after round r, gs[c] is the
-// sum of dA over the first 2^r cells of c's in-tile path, nx[c] the next cell
-// not yet included (or NX_END) and en[c] the last cell included.  Converges in
-// ceil(log2(longest in-tile path)) rounds.  Returns the buffer holding the result.
+// In-tile path sums by synchronous pointer jumping.  Thread t owns the cells
+// t + NTB k and keeps their state (sum so far, next cell) in registers; two
+// shared buffers hold everyone's state for the gathers.  Round r reads buffer
+// r & 1 and, for each owned cell c still open, sets sum(c) += sum(a),
+// next(c) = next(a) with a = next(c), written to the other buffer; after
+// round r an open cell's sum covers the first 2^(r+1) cells of its path.  A
+// cell is closed once next(c) carries NX_DONE (its sum then reaches its tile
+// exit or path end); it copies its final state into the other buffer once,
+// in the round after it closed, and is never touched again, so a round costs
+// only the cells still open.  Cells that start closed are written to both
+// buffers, so after the last round the buffer written last is final
+// everywhere.
 template <int T>
-__device__ int tile_path_sums(const DemDesc& d, const TileGeo& g, unsigned char* sm, uint32_t* status) {
-  using L = BwdLayout<T>;
-  ff* gs = reinterpret_cast<ff*>(sm + L::off_gs);
-  uint16_t* nx = reinterpret_cast<uint16_t*>(sm + L::off_nx);
-  uint16_t* en = reinterpret_cast<uint16_t*>(sm + L::off_en);
-  uint8_t* cl = sm + L::off_cl;
-  constexpr int TT = T * T;
-  for (int c = threadIdx.x; c < TT; c += NT) {
-    const int i = c / T, j = c - i * T;
-    uint16_t n = NX_END;
-    ff v{0.0f, 0.0f};
-    if (i >= g.th || j >= g.tw) {
-      cl[c] = CL_ABSENT;
-    } else {
-      const int64_t gi = g.i0 + i, gj = g.j0 + j;
-      const uint8_t f = classify(d.dir[gi * d.lddir + gj], i, j, g, d, status);
-      cl[c] = f;
-      if (f & CL_IN) {
-        const int k = f & 7;
-        n = (uint16_t)(c + code_di(k) * T + code_dj(k));
-      }
-      v.hi = d.w[gi * d.ldw + gj];
-    }
-    gs[c] = v;
-    nx[c] = n;
-    en[c] = (uint16_t)c;
-  }
-  __syncthreads();
-  int b = 0;
-  bool any = true;
-  for (int round = 0; round < 2 * 14 + 2 && any; round++) {
-    bool act = false;
-    const ff* gsb = gs + b * TT;
-    const uint16_t* nxb = nx + b * TT;
-    const uint16_t* enb = en + b * TT;
-    ff* gso = gs + (b ^ 1) * TT;
-    uint16_t* nxo = nx + (b ^ 1) * TT;
-    uint16_t* eno = en + (b ^ 1) * TT;
-    for (int c = threadIdx.x; c < TT; c += NT) {
-      const uint16_t a = nxb[c];
-      if (a == NX_END) {
-        gso[c] = gsb[c];
-        nxo[c] = NX_END;
-        eno[c] = enb[c];
-      } else {
-        gso[c] = ff_add(gsb[c], gsb[a]);
-        const uint16_t na = nxb[a];
-        nxo[c] = na;
-        eno[c] = enb[a];
-        act |= (na != NX_END);
-      }
-    }
-    b ^= 1;
-    any = __syncthreads_or(act);
-  }
-  if (any && threadIdx.x == 0) set_status(status, D8_ERR_CYCLE);
-  return b;
-}
-
-template <int T>
-__global__ void __launch_bounds__(NT) k_bwd_up(DemTable dt, Pipe p) {
+__global__ void __launch_bounds__(BwdCfg<T>::NTB, T >= 64 ? 2 : 4) k_bwd_up(DemTable dt, Pipe p) {
+  constexpr int NTB = BwdCfg<T>::NTB, CPT = BwdCfg<T>::CPT, TT = T * T;
   using L = BwdLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
   ff* gs = reinterpret_cast<ff*>(sm + L::off_gs);
-  uint16_t* en = reinterpret_cast<uint16_t*>(sm + L::off_en);
-  const uint8_t* cl = sm + L::off_cl;
+  uint16_t* nx = reinterpret_cast<uint16_t*>(sm + L::off_nx);
+  uint8_t* cl = sm + L::off_cl;
   ff* pval = static_cast<ff*>(p.pval);
-  constexpr int TT = T * T;
   TileQueue tq(p.queue + 2, p.ntiles);
   for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
-    const int b = tile_path_sums<T>(d, g, sm, p.status);
-    for (int s = threadIdx.x; s < 4 * T; s += NT) {
+    // this thread's cells are (i0 + k * NTB / T, j) for k = 0 .. CPT-1: row
+    // pointers step by NTB / T rows; all loads issued before any is used
+    const int i0 = threadIdx.x / T, j = threadIdx.x % T;
+    constexpr int RS = NTB / T;  // rows between a thread's cells
+    const bool colin = j < g.tw;
+    const uint8_t* dp = d.dir + (g.i0 + i0) * d.lddir + (g.j0 + j);
+    const float* wp = d.w + (g.i0 + i0) * d.ldw + (g.j0 + j);
+    uint8_t code[CPT];
+    float w[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+      code[k] = 0;
+      w[k] = 0.0f;
+      if (colin && i0 + k * RS < g.th) {
+        code[k] = dp[(int64_t)k * RS * d.lddir];
+        w[k] = wp[(int64_t)k * RS * d.ldw];
+      }
+    }
+    ff v[CPT];
+    uint32_t n[CPT];
+    uint32_t open = 0;
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+      const int c = threadIdx.x + k * NTB, i = i0 + k * RS;
+      uint8_t f = CL_ABSENT;
+      n[k] = NX_DONE | (uint32_t)c;
+      if (colin && i < g.th) {
+        // class of the code: in-tile target (local test), else exit or path
+        // end (grid test, perimeter cells only)
+        const int kk = code[k];
+        if (kk >= 8) {
+          f = CL_TERM;
+          if (kk > 9) set_status(p.status, D8_ERR_ARG);
+        } else {
+          const int li = i + code_di(kk), lj = j + code_dj(kk);
+          if ((unsigned)li < (unsigned)g.th && (unsigned)lj < (unsigned)g.tw) {
+            f = (uint8_t)(CL_IN | kk);
+            n[k] = (uint32_t)(li * T + lj);
+            open |= 1u << k;
+          } else {
+            const int64_t gi = g.i0 + li, gj = g.j0 + lj;
+            f = (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) ? CL_TERM : (uint8_t)(CL_EXIT | kk);
+          }
+        }
+      }
+      v[k] = ff{w[k], 0.0f};
+      cl[c] = f;
+      gs[c] = v[k];
+      nx[c] = (uint16_t)n[k];
+      if (!((open >> k) & 1u)) {
+        gs[TT + c] = v[k];
+        nx[TT + c] = (uint16_t)n[k];
+      }
+    }
+    bool any = __syncthreads_or(open != 0);
+    int b = 0;
+    uint32_t closed = 0;  // cells that closed in the previous round
+    for (int round = 0; any && round < BwdCfg<T>::MAXR; round++) {
+      const ff* gsb = gs + b * TT;
+      const uint16_t* nxb = nx + b * TT;
+      ff* gso = gs + (b ^ 1) * TT;
+      uint16_t* nxo = nx + (b ^ 1) * TT;
+      uint32_t now = 0;
+#pragma unroll
+      for (int k = 0; k < CPT; k++) {
+        const int c = threadIdx.x + k * NTB;
+        if ((open >> k) & 1u) {
+          const uint32_t na = nxb[n[k]];
+          v[k] = ff_add(v[k], gsb[n[k]]);
+          n[k] = na;
+          gso[c] = v[k];
+          nxo[c] = (uint16_t)na;
+          if (na & NX_DONE) now |= 1u << k;
+        } else if ((closed >> k) & 1u) {
+          gso[c] = v[k];
+          nxo[c] = (uint16_t)n[k];
+        }
+      }
+      open &= ~now;
+      closed = now;
+      b ^= 1;
+      any = __syncthreads_or(open != 0);
+    }
+    const ff* gsf = gs + b * TT;  // final everywhere
+    const uint16_t* nxf = nx + b * TT;
+    if (any && threadIdx.x == 0) set_status(p.status, D8_ERR_CYCLE);
+    // perimeter summary from the final shared state
+    for (int s = threadIdx.x; s < 4 * T; s += NTB) {
       int i, j;
       uint16_t pe = PEX_TERM;
-      ff v{0.0f, 0.0f};
+      ff pv{0.0f, 0.0f};
       if (slot_cell(s, g.th, g.tw, T, i, j)) {
         const int c = i * T + j;
-        const int e = en[b * TT + c];
+        const int e = nxf[c] & (TT - 1);
         if (cl[e] & CL_EXIT) pe = (e == c) ? (uint16_t)(PEX_EXIT | (cl[c] & 7)) : (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T);
-        v = gs[b * TT + c];
+        pv = gsf[c];
       }
       p.pex[t * (4 * T) + s] = pe;
-      pval[t * (4 * T) + s] = v;
+      pval[t * (4 * T) + s] = pv;
     }
-    // every cell: its in-tile path sum (to dw) and its exit's slot
-    for (int c = threadIdx.x; c < TT; c += NT) {
-      const int i = c / T, j = c - i * T;
-      if (i >= g.th || j >= g.tw) continue;
-      const ff v = gs[b * TT + c];
-      const int e = en[b * TT + c];
-      const int64_t gi = g.i0 + i, gj = g.j0 + j;
-      static_cast<float*>(d.A)[gi * d.ldA + gj] = __fadd_rn(v.hi, v.lo);
-      p.xid[gi * d.W + gj] = (cl[e] & CL_EXIT) ? (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T) : NO_EXIT;
+    // every owned cell: its in-tile path sum (to dw) and its exit's slot
+    float* ap = static_cast<float*>(d.A) + (g.i0 + i0) * d.ldA + (g.j0 + j);
+    uint16_t* xp = p.xid + (g.i0 + i0) * d.W + (g.j0 + j);
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+      if (!colin || i0 + k * RS >= g.th) continue;
+      const int e = n[k] & (TT - 1);
+      ap[(int64_t)k * RS * d.ldA] = __fadd_rn(v[k].hi, v[k].lo);
+      xp[(int64_t)k * RS * d.W] = (cl[e] & CL_EXIT) ? (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T) : NO_EXIT;
     }
     __syncthreads();
   }
 }
 
+// Append the lanes whose `take` is set to list[] at the position counter
+// *cnt hands out (one atomic per warp); every lane of the warp calls this.
+__device__ __forceinline__ void warp_append(bool take, uint32_t item, uint32_t* list, uint32_t* cnt) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  uint32_t pos = 0;
+  if (lane == leader) pos = atomicAdd(cnt, (uint32_t)__popc(m));
+  pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+  if (take) list[pos + __popc(m & ((1u << lane) - 1u))] = item;
+}
+
 // combine init: H0(x) = path sum of x's successor inside its tile, parent =
-// the exit that successor's path reaches
+// the exit that successor's path reaches.  Slots without a parent are final
+// now and go to both value buffers; the others are listed for round 0
+// (flags[r] counts the list of round r).
 template <int T>
 __global__ void k_bpj_init(DemTable dt, Pipe p) {
   ff* H = static_cast<ff*>(p.S);
+  ff* H2 = static_cast<ff*>(p.S2);
   const ff* pval = static_cast<const ff*>(p.pval);
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < p.nslots; g += stride) {
-    const uint16_t pe = p.pex[g];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < p.nslots; base += stride) {
+    const int64_t g = base + lane;
     uint32_t par = ROOT;
-    ff v{0.0f, 0.0f};
-    if (pe & PEX_EXIT) {
-      const int64_t t = g / (4 * T);
-      const int s = (int)(g - t * (4 * T));
-      const DemDesc d = dem_of(dt, t);
-      const TileGeo geo = tile_geo(d, t - d.tile_base, T);
-      int i, j;
-      slot_cell(s, geo.th, geo.tw, T, i, j);
-      const int k = pe & 7;
-      const int64_t y = global_slot(d, geo.i0 + i + code_di(k), geo.j0 + j + code_dj(k), T);
-      const uint16_t pey = p.pex[y];
-      if (pey & PEX_EXIT)
-        par = (uint32_t)y;
-      else if (pey != PEX_TERM)
-        par = (uint32_t)((y / (4 * T)) * (4 * T) + pey);
-      v = pval[y];
-      if (par != ROOT) p.flags[0] = 1u;
+    if (g < p.nslots) {
+      const uint16_t pe = p.pex[g];
+      ff v{0.0f, 0.0f};
+      if (pe & PEX_EXIT) {
+        const int64_t t = g / (4 * T);
+        const int s = (int)(g - t * (4 * T));
+        const DemDesc d = dem_of(dt, t);
+        const TileGeo geo = tile_geo(d, t - d.tile_base, T);
+        int i, j;
+        slot_cell(s, geo.th, geo.tw, T, i, j);
+        const int k = pe & 7;
+        const int64_t y = global_slot(d, geo.i0 + i + code_di(k), geo.j0 + j + code_dj(k), T);
+        const uint16_t pey = p.pex[y];
+        if (pey & PEX_EXIT)
+          par = (uint32_t)y;
+        else if (pey != PEX_TERM)
+          par = (uint32_t)((y / (4 * T)) * (4 * T) + pey);
+        v = pval[y];
+      }
+      p.P[0][g] = par;
+      H[g] = v;
+      if (par == ROOT) {
+        p.P[1][g] = ROOT;
+        H2[g] = v;
+      }
     }
-    p.P[0][g] = par;
-    H[g] = v;
+    warp_append(par != ROOT, (uint32_t)g, p.list[0], &p.flags[0]);
   }
 }
 
-// one round of path doubling: H <- H + H(parent), parent <- parent(parent)
+// One round of path doubling over the listed exits: H <- H + H(parent),
+// parent <- parent(parent), written to the other buffers.  An exit whose
+// parent became ROOT is listed once more, for a round that only copies its
+// final H into the other buffer, so that both buffers end up final for every
+// slot (a later round may gather it from either).  The grid-stride loop runs
+// the same number of times in every lane of a warp (the stride is a multiple
+// of 32), as warp_append requires.
 __global__ void k_bpj_round(Pipe p, int r) {
-  if (*(volatile uint32_t*)&p.flags[r] == 0u) return;
+  const uint32_t n = *(volatile uint32_t*)&p.flags[r];
+  if (n == 0u) return;
   const ff* Hc = static_cast<const ff*>((r & 1) ? p.S2 : p.S);
   ff* Hn = static_cast<ff*>((r & 1) ? p.S : p.S2);
   const uint32_t* Pc = pick(p.P[0], p.P[1], r & 1);
   uint32_t* Pn = pick(p.P[0], p.P[1], (r + 1) & 1);
+  const uint32_t* lc = p.list[r & 1];
+  uint32_t* ln = p.list[(r + 1) & 1];
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  bool active = false;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < p.nslots; g += stride) {
-    const uint32_t par = Pc[g];
-    ff h = Hc[g];
-    uint32_t pp = ROOT;
-    if (par != ROOT) {
-      h = ff_add(h, Hc[par]);
-      pp = Pc[par];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < (int64_t)n; base += stride) {
+    const int64_t i = base + lane;
+    bool keep = false;
+    uint32_t g = 0;
+    if (i < (int64_t)n) {
+      g = lc[i];
+      const uint32_t par = Pc[g];
+      ff h = Hc[g];
+      uint32_t pp = ROOT;
+      if (par != ROOT) {
+        h = ff_add(h, Hc[par]);
+        pp = Pc[par];
+        keep = true;
+      }
+      Hn[g] = h;
+      Pn[g] = pp;
     }
-    Hn[g] = h;
-    Pn[g] = pp;
-    active |= (pp != ROOT);
+    warp_append(keep, g, ln, &p.flags[r + 1]);
   }
-  if (__syncthreads_or(active) && threadIdx.x == 0) p.flags[r + 1] = 1u;
-  if (blockIdx.x == 0 && threadIdx.x == 0) p.flags[MAX_ROUNDS + 1] = (uint32_t)(r + 1);
 }
 
+// after R rounds the list must be empty; an exit still open lies on a cycle
 __global__ void k_bpj_check(Pipe p, int R) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && p.flags[R] != 0u) set_status(p.status, D8_ERR_CYCLE);
 }
@@ -215,8 +290,7 @@ __global__ void k_bpj_check(Pipe p, int R) {
 template <int T, bool VEC>
 __global__ void k_bwd_fix(DemTable dt, Pipe p) {
   const DemDesc d = dt.one;
-  const uint32_t last = *(volatile uint32_t*)&p.flags[MAX_ROUNDS + 1];
-  const ff* H = static_cast<const ff*>((last & 1) ? p.S2 : p.S);
+  const ff* H = static_cast<const ff*>(p.S);  // final in both buffers
   constexpr int V = VEC ? 4 : 1;
   const int64_t wq = d.W / V;  // groups per row
   const int64_t n = d.H * wq;
@@ -259,11 +333,11 @@ __global__ void k_bwd_fix(DemTable dt, Pipe p) {
 // ---------------------------------------------------------------------------
 
 template <class K>
-static unsigned persistent_grid_b(K kernel, size_t smem, int64_t ntiles) {
+static unsigned persistent_grid_b(K kernel, int threads, size_t smem, int64_t ntiles) {
   int dev = 0, sms = 1, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -272,22 +346,22 @@ static unsigned persistent_grid_b(K kernel, size_t smem, int64_t ntiles) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-static unsigned grid_for_b(int64_t n) {
+static unsigned grid_for_b(int64_t n, int per_sm) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t b = (n + 255) / 256;
-  if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
+  if (b > (int64_t)sms * per_sm) b = (int64_t)sms * per_sm;
   return (unsigned)(b < 1 ? 1 : b);
 }
 
 template <int T>
 static cudaError_t launch_bwd_up_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
   const size_t bytes = BwdLayout<T>::bytes;
-  if (bytes > 227 * 1024) return cudaErrorInvalidValue;
+  constexpr int NTB = BwdCfg<T>::NTB;
   cudaError_t e = cudaFuncSetAttribute(k_bwd_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  k_bwd_up<T><<<persistent_grid_b(k_bwd_up<T>, bytes, p.ntiles), NT, bytes, s>>>(dt, p);
+  k_bwd_up<T><<<persistent_grid_b(k_bwd_up<T>, NTB, bytes, p.ntiles), NTB, bytes, s>>>(dt, p);
   return cudaGetLastError();
 }
 
@@ -295,17 +369,11 @@ template <int T>
 static cudaError_t launch_bwd_fix_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
   const DemDesc& d = dt.one;
   const bool vec = d.W % 4 == 0 && d.ldA % 4 == 0 && (reinterpret_cast<uintptr_t>(d.A) & 15u) == 0;
-  const int64_t n = d.H * (vec ? d.W / 4 : d.W);
-  int64_t b = (n + 255) / 256;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (b > (int64_t)sms * 32) b = (int64_t)sms * 32;
-  if (b < 1) b = 1;
+  const unsigned b = grid_for_b(d.H * (vec ? d.W / 4 : d.W), 32);
   if (vec)
-    k_bwd_fix<T, true><<<(unsigned)b, 256, 0, s>>>(dt, p);
+    k_bwd_fix<T, true><<<b, 256, 0, s>>>(dt, p);
   else
-    k_bwd_fix<T, false><<<(unsigned)b, 256, 0, s>>>(dt, p);
+    k_bwd_fix<T, false><<<b, 256, 0, s>>>(dt, p);
   return cudaGetLastError();
 }
 
@@ -318,18 +386,24 @@ cudaError_t launch_bwd_up(const DemTable& dt, const Pipe& p, cudaStream_t s, int
   return cudaErrorInvalidValue;
 }
 
+// Rounds R = rounds + 2: any chain of the exit forest closes within `rounds`
+// (2^rounds > slot count), and the copy round of the last exits to close
+// comes one round later, so the list of round R is empty unless a cycle holds
+// exits open.  Rounds after the list empties return at once.
 template <int T>
 static cudaError_t launch_combine_bwd_t(const DemTable& dt, const Pipe& p, cudaStream_t s, int* nlaunch) {
+  const int R = p.rounds + 2;
+  if (R > MAX_ROUNDS + 1) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(p.flags, 0, sizeof(uint32_t) * (MAX_ROUNDS + 2), s);
   if (e != cudaSuccess) return e;
-  const unsigned gb = grid_for_b(p.nslots);
-  k_bpj_init<T><<<gb, 256, 0, s>>>(dt, p);
+  k_bpj_init<T><<<grid_for_b(p.nslots, 16), 256, 0, s>>>(dt, p);
   ++*nlaunch;
-  for (int r = 0; r < p.rounds; r++) {
-    k_bpj_round<<<gb, 256, 0, s>>>(p, r);
+  const unsigned gr = grid_for_b(p.nslots, 8);
+  for (int r = 0; r < R; r++) {
+    k_bpj_round<<<gr, 256, 0, s>>>(p, r);
     ++*nlaunch;
   }
-  k_bpj_check<<<1, 32, 0, s>>>(p, p.rounds);
+  k_bpj_check<<<1, 32, 0, s>>>(p, R);
   ++*nlaunch;
   return cudaGetLastError();
 }

@@ -66,6 +66,7 @@ struct Pipe {
   uint32_t* status;  // device status word (OR of 1 << d8_status)
   uint32_t* queue;   // tile work-queue counters (one per stage)
   uint16_t* xid;     // adjoint only: per cell (row-major, W per row) the slot of its tile exit, or NO_EXIT
+  uint32_t* list[2]; // adjoint only: the exits still open in the combine's rounds (even / odd)
   const uint32_t* top_in;  // unit counts: inflow entering row 0 from above, per column (or null)
   const uint32_t* bot_in;  // unit counts: inflow entering row H-1 from below, per column (or null)
 };
@@ -140,6 +141,5 @@ cudaError_t run_fill(const float* z, int64_t H, int64_t W, int64_t ldz, float ep
 // shared-memory bytes of the per-tile kernels (0 = configuration unsupported)
 size_t up_smem_bytes(int T, int mode);
 size_t down_smem_bytes(int T, bool weighted);
-size_t bwd_smem_bytes(int T);
 
 }  // namespace d8

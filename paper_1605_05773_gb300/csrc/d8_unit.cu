@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(Dem
         // same iteration, so the refill and hand-out above are paid once per
         // two steps of the long walks
 #pragma unroll
-        for (int k = 0; k < (WT ? 1 : UNIT_STEPS); k++) {
+        for (int k = 0; k < (WT ? 2 : UNIT_STEPS); k++) {
           if (cur < 0) break;
           if (WT) {
             val[cur] = v;

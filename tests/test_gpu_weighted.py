@@ -132,3 +132,49 @@ def test_weighted_top_level_strategies(d8, strategy):
             assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
     finally:
         d8.set_strategy("ring")
+
+
+@pytest.mark.parametrize("T", [32, 64])
+def test_backward_long_exit_chains(d8, T):
+    """A serpentine field: one path through every cell, so the exit forest of
+    the adjoint's combine is a single chain crossing tile borders tens of
+    thousands of times (many pointer-jumping rounds).  With c = 1 the gradient
+    is the path length, exact in fp32; with c ~ N(0, 1) within the bar."""
+    d8.set_tile(T)
+    try:
+        f = demgen.serpentine_dirs(1536, 1024)
+        H, W = f.shape
+        g = d8.accumulate_backward(to_dev(f), torch.ones((H, W), device="cuda")).cpu().numpy()
+        np.testing.assert_array_equal(g, oracle.transposed(f, np.ones((H, W))).astype(np.float32))
+        c = demgen.normal_cotangent(H, W, seed=14)
+        g = d8.accumulate_backward(to_dev(f), to_dev(c)).cpu().numpy()
+        assert grad_error(g, f, c)[0] <= TOL
+        assert d8.get_status() == "OK"
+    finally:
+        d8.set_tile(64)
+
+
+@pytest.mark.parametrize("T", [32, 64])
+def test_backward_reports_cycles(d8, T):
+    """A 2-cycle inside a tile and a loop through two tiles (seen only by the
+    combine) both end with ERR_CYCLE; a valid field afterwards is clean."""
+    d8.set_tile(T)
+    try:
+        cyc = np.full((40, 50), 8, dtype=np.uint8)
+        cyc[10, 10], cyc[10, 11] = 2, 6
+        d8.accumulate_backward(to_dev(cyc), torch.ones((40, 50), device="cuda"))
+        assert d8.get_status() == "ERR_CYCLE"
+        big = np.full((96, 150), 8, dtype=np.uint8)
+        big[10, 10:100] = 2
+        big[10, 100] = 4
+        big[11, 11:101] = 6
+        big[11, 10] = 0
+        d8.accumulate_backward(to_dev(big), torch.ones((96, 150), device="cuda"))
+        assert d8.get_status() == "ERR_CYCLE"
+        ok = np.full((96, 150), 8, dtype=np.uint8)
+        ok[10, 10:100] = 2
+        g = d8.accumulate_backward(to_dev(ok), torch.ones((96, 150), device="cuda")).cpu().numpy()
+        assert d8.get_status() == "OK"
+        np.testing.assert_array_equal(g, oracle.transposed(ok, np.ones((96, 150))).astype(np.float32))
+    finally:
+        d8.set_tile(64)
