@@ -138,9 +138,13 @@ d8_status d8_accumulate_inflow(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64
 
 /* Weighted up-slope area A(p) = w(p) + sum of A over the cells draining into
  * p (Eq. 1 with the paragraph after it: cells "may or may not be weighted
- * equally").  fp32 in and out, compensated (TwoSum) fp32 accumulation
- * throughout.  w: H x W (ld ldw); A: H x W (ld ldA).  Errors as
- * d8_accumulate. */
+ * equally").  fp32 in and out.  Sums are float-float (TwoSum-compensated
+ * fp32) inside tiles and across them; the inflow a tile receives is added
+ * along its paths in exact per-tile fixed point (78 value bits, scaled to the
+ * tile's summed inflow), so the result keeps fp32 accuracy across wide
+ * ranges of weights.  w: H x W (ld ldw); A: H x W (ld ldA).  Errors as
+ * d8_accumulate, plus D8_ERR_NONFINITE when a non-finite weight's area
+ * reaches another tile. */
 d8_status d8_accumulate_weighted(d8_ctx* ctx, const uint8_t* dir, int64_t H, int64_t W, int64_t lddir,
                                  const float* w, int64_t ldw, float* A, int64_t ldA, d8_stream stream);
 

@@ -163,20 +163,20 @@ struct FinLayout {
   static constexpr size_t bytes = off_misc + 64;
 };
 
-// finalising pass, weighted: float-float F per cell and a mark word per cell
-// (bits 0..7: which neighbours are inputs carrying inflow; 8..15: how many of
-// them are still to arrive; 16: the cell is a receiver)
+// finalising pass, weighted: the inflow routed through each cell as a
+// fixed-point number in three 32-bit words (FxLimbs; word 0 of every cell,
+// then word 1, then word 2)
 template <int T>
 struct FinWLayout {
   static constexpr size_t TT = (size_t)T * T;
-  static constexpr size_t off_f = 0;                     // ff per cell
-  static constexpr size_t off_mk = TT * sizeof(ff);      // uint32 per cell
-  static constexpr size_t off_code = off_mk + TT * 4;    // uint8 code per cell
+  static constexpr size_t off_w = 0;                     // uint32 [3][TT]
+  static constexpr size_t off_code = TT * 12;            // uint8 code per cell
   static constexpr size_t off_rcell = off_code + TT;     // uint16 per perimeter slot
-  static constexpr size_t off_misc = (off_rcell + (size_t)4 * T * 2 + 15) / 16 * 16;
+  static constexpr size_t off_rin = off_rcell + (size_t)4 * T * 2;  // ff per slot
+  static constexpr size_t off_ring = off_rin + (size_t)4 * T * sizeof(ff);  // uint8 codes around the tile
+  static constexpr size_t off_misc = (off_ring + 2 * (T + 2) + 2 * T + 15) / 16 * 16;
   static constexpr size_t bytes = off_misc + 64;
 };
-constexpr uint32_t MK_CNT1 = 1u << 8, MK_REC = 1u << 16;
 
 // Codes of tile g from a given direction field into word[], four consecutive
 // cells per thread per step (one 32-bit load when the layout allows); for a
@@ -578,6 +578,64 @@ __global__ void __launch_bounds__(NTU, 8) k_up_lm(DemTable dt, Pipe p) {
   }
 }
 
+// The codes of tile g copied straight into code[] (16 at a time, by
+// asynchronous copies when the rows allow) and the codes of the one-cell ring
+// around it into ring[] (top T+2, bottom T+2, left T, right T; 0xFF off the
+// grid), all requested before any is waited for.  Returns once this thread's
+// copies have landed; the caller's barrier makes them visible to the block.
+template <int T>
+__device__ __forceinline__ void fin_codes(const DemDesc& d, const TileGeo& g, uint8_t* code, uint8_t* ring) {
+  constexpr int TT = T * T;
+  const bool vecD = g.tw == T && ((reinterpret_cast<uintptr_t>(d.dir) & 15u) == 0) && (d.lddir % 16 == 0);
+  for (int q = threadIdx.x; q < TT / 16; q += NTF) {  // 16 codes at a time
+    const int c = q * 16, i = c / T, j = c - i * T;
+    uint8_t* dst = code + c;
+    if (i >= g.th) {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0x08080808u, 0x08080808u, 0x08080808u, 0x08080808u);
+      continue;
+    }
+    const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
+    if (vecD) {
+      cp_async16(dst, src, 16);
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < 16; k++) dst[k] = j + k < g.tw ? src[k] : (uint8_t)8;
+    }
+  }
+  cp_async_commit();
+  for (int q = threadIdx.x; q < 2 * (T + 2) + 2 * T; q += NTF) {
+    int li, lj;
+    if (q < T + 2) {
+      li = -1;
+      lj = q - 1;
+    } else if (q < 2 * (T + 2)) {
+      li = g.th;
+      lj = q - (T + 2) - 1;
+    } else if (q < 2 * (T + 2) + T) {
+      li = q - 2 * (T + 2);
+      lj = -1;
+    } else {
+      li = q - 2 * (T + 2) - T;
+      lj = g.tw;
+    }
+    const int64_t gi = g.i0 + li, gj = g.j0 + lj;
+    uint8_t v = 0xFF;
+    if (gi >= 0 && gj >= 0 && gi < d.H && gj < d.W && li <= g.th && lj <= g.tw && (q < 2 * (T + 2) || li < g.th))
+      v = d.dir[gi * d.lddir + gj];
+    ring[q] = v;
+  }
+  cp_async_wait<0>();
+}
+
+// code of the cell (li, lj) just outside tile g, from the ring
+template <int T>
+__device__ __forceinline__ uint32_t fin_ring_code(const uint8_t* ring, const TileGeo& g, int li, int lj) {
+  if (li < 0) return ring[lj + 1];
+  if (li >= g.th) return ring[(T + 2) + lj + 1];
+  if (lj < 0) return ring[2 * (T + 2) + li];
+  return ring[2 * (T + 2) + T + li];
+}
+
 // Algorithms 7-8 restricted to where they change anything.  The final count
 // is A(c) + F(c), where A holds the in-tile counts and F(c) is the inflow
 // from other tiles routed through c.  Inflow enters a tile only at its
@@ -618,58 +676,9 @@ __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
     if (threadIdx.x == 0) misc[0] = 0;
-    // the tile's codes copied straight into shared memory, and the codes of
-    // the ring around it, all requested before any is waited for
-    {
-      const bool vecD = g.tw == T && ((reinterpret_cast<uintptr_t>(d.dir) & 15u) == 0) && (d.lddir % 16 == 0);
-      for (int q = threadIdx.x; q < TT / 16; q += NTF) {  // 16 codes at a time
-        const int c = q * 16, i = c / T, j = c - i * T;
-        uint8_t* dst = code + c;
-        if (i >= g.th) {
-          *reinterpret_cast<uint4*>(dst) = make_uint4(0x08080808u, 0x08080808u, 0x08080808u, 0x08080808u);
-          continue;
-        }
-        const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
-        if (vecD) {
-          cp_async16(dst, src, 16);
-        } else {
-#pragma unroll 4
-          for (int k = 0; k < 16; k++) dst[k] = j + k < g.tw ? src[k] : (uint8_t)8;
-        }
-      }
-      cp_async_commit();
-      // the ring of codes around the tile (0xFF off the grid)
-      for (int q = threadIdx.x; q < 2 * (T + 2) + 2 * T; q += NTF) {
-        int li, lj;
-        if (q < T + 2) {
-          li = -1;
-          lj = q - 1;
-        } else if (q < 2 * (T + 2)) {
-          li = g.th;
-          lj = q - (T + 2) - 1;
-        } else if (q < 2 * (T + 2) + T) {
-          li = q - 2 * (T + 2);
-          lj = -1;
-        } else {
-          li = q - 2 * (T + 2) - T;
-          lj = g.tw;
-        }
-        const int64_t gi = g.i0 + li, gj = g.j0 + lj;
-        uint8_t v = 0xFF;
-        if (gi >= 0 && gj >= 0 && gi < d.H && gj < d.W && li <= g.th && lj <= g.tw && (q < 2 * (T + 2) || li < g.th))
-          v = d.dir[gi * d.lddir + gj];
-        ring[q] = v;
-      }
-      cp_async_wait<0>();
-    }
+    fin_codes<T>(d, g, code, ring);
     __syncthreads();
     // Algorithm 7: the receivers and their resolved inflow, listed
-    auto ring_code = [&](int li, int lj) -> uint32_t {  // code of a cell just outside the tile
-      if (li < 0) return ring[lj + 1];
-      if (li >= g.th) return ring[(T + 2) + lj + 1];
-      if (lj < 0) return ring[2 * (T + 2) + li];
-      return ring[2 * (T + 2) + T + li];
-    };
     for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
@@ -679,7 +688,7 @@ __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
       for (int k = 0; k < 8; k++) {
         const int li = i + code_di(k), lj = j + code_dj(k);
         if (li >= 0 && lj >= 0 && li < g.th && lj < g.tw) continue;
-        if (ring_code(li, lj) != (uint32_t)opposite(k)) continue;  // also rejects cells off the grid
+        if (fin_ring_code<T>(ring, g, li, lj) != (uint32_t)opposite(k)) continue;  // also rejects cells off the grid
         in += xval[global_slot(d, g.i0 + li, g.j0 + lj, T)];
         any = true;
       }
@@ -745,62 +754,152 @@ __global__ void __launch_bounds__(NTF, 8) k_fin_unit(DemTable dt, Pipe p) {
   }
 }
 
-// Algorithms 7-8 for weighted areas, on the same sub-forest (the receivers'
-// in-tile paths), without floating-point atomics (they are not native in
-// shared memory and converging paths would retry them): a marking walk from
-// each receiver counts, per reached cell, its inputs that carry inflow and
-// which neighbours they are, stopping where the cell was already reached or
-// is a receiver itself; the receivers with no such input are noted; then the
-// inflow is propagated in dependency order, each cell's float-float F being
-// its own inflow plus its inputs' F pulled in N..NW order (deterministic),
-// published behind block fences as in the tile pass.  A = fp32(A + F).
+// 96-bit two's-complement fixed point, three 32-bit words (w0 lowest).
+struct fx96 {
+  uint32_t w0, w1, w2;
+};
+
+// round(f * 2^q) (ties away from zero) for a finite f with |f| 2^q < 2^94
+__device__ __forceinline__ fx96 fx96_of(float f, int q) {
+  const uint32_t bits = __float_as_uint(f);
+  const int E = (int)((bits >> 23) & 0xFFu);
+  const uint32_t mant = (bits & 0x7FFFFFu) | (E ? 0x800000u : 0u);
+  const int s = (E ? E : 1) - 150 + q;  // f * 2^q = mant * 2^s
+  uint64_t lo = 0;
+  uint32_t hi = 0;
+  if (mant != 0u) {
+    if (s >= 64) {
+      hi = mant << (s - 64);
+    } else if (s >= 0) {
+      lo = (uint64_t)mant << s;
+      hi = s > 40 ? (uint32_t)(mant >> (64 - s)) : 0u;
+    } else if (s > -26) {
+      lo = ((uint64_t)mant + (1ull << (-s - 1))) >> (-s);
+    }
+  }
+  if (bits >> 31) {  // negate the 96-bit value
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1u : 0u);
+  }
+  return fx96{(uint32_t)lo, (uint32_t)(lo >> 32), hi};
+}
+
+__device__ __forceinline__ fx96 fx96_add(fx96 a, fx96 b) {
+  const uint64_t al = a.w0 | ((uint64_t)a.w1 << 32), bl = b.w0 | ((uint64_t)b.w1 << 32);
+  const uint64_t l = al + bl;
+  return fx96{(uint32_t)l, (uint32_t)(l >> 32), a.w2 + b.w2 + (l < al ? 1u : 0u)};
+}
+
+// The finalise's per-cell fixed-point accumulator: word 0 is the low 32 bits,
+// summed modulo 2^32 with the carry of each addition taken from the atomic's
+// reply; words 1 and 2 are limbs of LB bits (unsigned, then signed) summed
+// without carries, their spare bits absorbing up to 4T additions (one per
+// receiver).  A value x with |x| < 2^(32 + 2 LB) enters as x0 = x mod 2^32,
+// x1 = (x >> 32) mod 2^LB, x2 = x >> (32 + LB); the three words then hold the
+// exact sum as w0 + w1 2^32 + w2 2^(32 + LB), whatever the order.
 template <int T>
-__global__ void __launch_bounds__(NTF, 4) k_fin_w(DemTable dt, Pipe p) {
+struct FxLimbs {
+  static constexpr int LB = T >= 128 ? 22 : (T >= 64 ? 23 : 24);  // 4T (LB-bit limb + carry) sums < 2^31
+  static constexpr int VB = 32 + 2 * LB;                          // value bits, sign included
+};
+
+template <int T>
+__device__ __forceinline__ void fx_split(fx96 v, uint32_t& x0, uint32_t& x1, uint32_t& x2) {
+  constexpr int LB = FxLimbs<T>::LB;
+  const long long rest = (long long)(v.w1 | ((unsigned long long)v.w2 << 32));  // v >> 32, |rest| < 2^(2 LB)
+  x0 = v.w0;
+  x1 = (uint32_t)rest & ((1u << LB) - 1u);
+  x2 = (uint32_t)(int)(rest >> LB);
+}
+
+// the three words of a cell back to a 96-bit two's-complement value
+template <int T>
+__device__ __forceinline__ fx96 fx_join(uint32_t w0, uint32_t w1, uint32_t w2) {
+  constexpr int LB = FxLimbs<T>::LB;
+  const uint64_t lo = (uint64_t)w0 + ((uint64_t)w1 << 32);  // w1 < 2^31
+  const long long t = (long long)(int)w2;                  // signed sum of the top limbs
+  const uint64_t tl = (uint64_t)t << (32 + LB);
+  const fx96 a{(uint32_t)lo, (uint32_t)(lo >> 32), 0u};
+  const fx96 b{(uint32_t)tl, (uint32_t)(tl >> 32), (uint32_t)(t >> (32 - LB))};
+  return fx96_add(a, b);
+}
+
+// The fixed-point value (w0, w1, w2) * 2^-q as float-float: the top 62 bits
+// of the magnitude rounded to fp32, plus their exact remainder rounded to
+// fp32 (a relative error of at most 2^-48 from the remainder's rounding and
+// 2^-61 from the bits below the top 62).
+__device__ __forceinline__ ff fx96_to_ff(uint32_t w0, uint32_t w1, uint32_t w2, int q) {
+  uint64_t lo = w0 | ((uint64_t)w1 << 32);
+  uint32_t hi = w2;
+  const bool neg = (hi >> 31) != 0u;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1u : 0u);
+  }
+  const int p = hi ? 95 - __clz(hi) : (lo ? 63 - __clzll(lo) : 0);  // leading bit
+  int sh = 0;
+  uint64_t U = lo;
+  if (p > 61) {
+    sh = p - 61;
+    U = (lo >> sh) | (hi ? ((uint64_t)hi << (64 - sh)) : 0ull);
+  }
+  const float fh = __ull2float_rn(U);  // U < 2^62 rounded to 24 bits: an integer
+  const float fl = __ll2float_rn((long long)(U - __float2ull_rn(fh)));
+  const ff r{ldexpf(fh, sh - q), ldexpf(fl, sh - q)};
+  return neg ? ff{-r.hi, -r.lo} : r;
+}
+
+// Algorithms 7-8 for weighted areas, on the same sub-forest and with the same
+// walks as the unit finalise.  The inflow is added in fixed point so that the
+// additions stay exact and commute: F(c) is an integer in units of 2^-q held
+// in three 32-bit words (FxLimbs: VB = 78 value bits for 64 x 64 tiles).  The
+// scale is set per tile from the receivers' inflows: with |in_r| < 2^e_r,
+// S = sum over receivers of 2^e_r (an exact integer sum of powers of two, so
+// the same in every run) bounds the sum of their magnitudes, and q makes
+// S * 2^q <= 2^(VB - 2), so that no partial sum reaches 2^(VB - 1) in
+// magnitude.  Each receiver's float-float inflow is rounded once to a
+// multiple of 2^-q, an error below 2^-q <= 2^-(VB - 4) * sum |in_r| (2^-74
+// for 64 x 64 tiles), far below fp32 resolution even when the tile's inflows
+// span twenty orders of magnitude; after that the sums are exact, so the
+// result does not depend on the schedule.  Finally A = fp32(A +
+// F), F converted to float-float.  A non-finite inflow (non-finite weights)
+// cannot be scaled: the tile keeps its in-tile areas and D8_ERR_NONFINITE is
+// raised.
+template <int T>
+__global__ void __launch_bounds__(NTF, T >= 64 ? 4 : 8) k_fin_w(DemTable dt, Pipe p) {
   using L = FinWLayout<T>;
   extern __shared__ __align__(16) unsigned char sm[];
-  ff* F = reinterpret_cast<ff*>(sm + L::off_f);
-  uint32_t* mk = reinterpret_cast<uint32_t*>(sm + L::off_mk);
+  uint32_t* F0 = reinterpret_cast<uint32_t*>(sm + L::off_w);  // words 0, 1, 2 at F0, F0 + TT, F0 + 2 TT
   uint8_t* code = sm + L::off_code;
   uint16_t* rcell = reinterpret_cast<uint16_t*>(sm + L::off_rcell);
-  int* misc = reinterpret_cast<int*>(sm + L::off_misc);
+  ff* rin = reinterpret_cast<ff*>(sm + L::off_rin);
+  uint8_t* ring = sm + L::off_ring;
+  uint32_t* misc = reinterpret_cast<uint32_t*>(sm + L::off_misc);
   const ff* xval = static_cast<const ff*>(p.S);
   constexpr int TT = T * T;
-  constexpr int RPT = (4 * T + NTF - 1) / NTF;  // receivers per thread at most
-  // in-tile down-slope cell of c, or -1
-  auto down = [&](int c, const TileGeo& g) -> int {
-    const int k = code[c];
-    if (k >= 8) return -1;
-    const int i = c / T + code_di(k), j = (c & (T - 1)) + code_dj(k);
-    return ((unsigned)i < (unsigned)g.th && (unsigned)j < (unsigned)g.tw) ? i * T + j : -1;
-  };
+  constexpr int NQ = TT / 4 / NTF > 0 ? TT / 4 / NTF : 1;  // quads per thread in the write-back
 
-  // F[] and mk[] (adjacent) start at zero; every tile leaves them at zero
-  for (int c = threadIdx.x; c < (int)(TT * (sizeof(ff) + 4) / 16); c += NTF)
-    reinterpret_cast<uint4*>(F)[c] = make_uint4(0, 0, 0, 0);
-  if (threadIdx.x == 0) misc[0] = 0;
-
+  // F starts at zero; every tile leaves the words it touched at zero again
+  for (int q = threadIdx.x; q < 3 * TT / 4; q += NTF) reinterpret_cast<uint4*>(F0)[q] = make_uint4(0, 0, 0, 0);
   TileQueue tq(p.queue + 1, p.ntiles);
   for (int64_t t = tq.first(); t < p.ntiles; t = tq.next()) {
     const DemDesc d = dem_of(dt, t);
     const TileGeo g = tile_geo(d, t - d.tile_base, T);
-    {
-      const bool vec = (g.tw == T) && ((reinterpret_cast<uintptr_t>(d.dir) & 3u) == 0) && (d.lddir % 4 == 0);
-      for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-        const int c = q * 4, i = c / T, j = c - i * T;
-        if (i >= g.th) continue;
-        const uint8_t* src = d.dir + (g.i0 + i) * d.lddir + (g.j0 + j);
-        uint32_t four = 0x08080808u;
-        if (vec) {
-          four = __ldg(reinterpret_cast<const unsigned int*>(src));
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; k++)
-            if (j + k < g.tw) four = (four & ~(0xFFu << (8 * k))) | ((uint32_t)src[k] << (8 * k));
-        }
-        reinterpret_cast<uint32_t*>(code)[q] = four;
-      }
+    unsigned long long* S = reinterpret_cast<unsigned long long*>(misc + 2);
+    if (threadIdx.x == 0) {
+      misc[0] = 0;  // receivers
+      misc[1] = 0;  // largest exponent bound, + 1024
+      misc[4] = 0;  // a non-finite inflow seen
+      *S = 0ull;
     }
-    // Algorithm 7: receivers, their inflow in F, marked
+    fin_codes<T>(d, g, code, ring);
+    __syncthreads();
+    // |x| < 2^ebound(x) for finite x (subnormals and zero: 2^-126)
+    auto ebound = [](float x) -> int {
+      const int eb = (int)((__float_as_uint(x) >> 23) & 0xFFu);
+      return eb == 0 ? -126 : eb - 126;
+    };
+    // Algorithm 7: the receivers and their resolved inflow, listed
     for (int s = threadIdx.x; s < 4 * T; s += NTF) {
       int i, j;
       if (!slot_cell(s, g.th, g.tw, T, i, j)) continue;
@@ -810,76 +909,83 @@ __global__ void __launch_bounds__(NTF, 4) k_fin_w(DemTable dt, Pipe p) {
       for (int k = 0; k < 8; k++) {
         const int li = i + code_di(k), lj = j + code_dj(k);
         if (li >= 0 && lj >= 0 && li < g.th && lj < g.tw) continue;
-        const int64_t gi = g.i0 + li, gj = g.j0 + lj;
-        if (gi < 0 || gj < 0 || gi >= d.H || gj >= d.W) continue;
-        if (d.dir[gi * d.lddir + gj] != opposite(k)) continue;
-        in = ff_add(in, xval[global_slot(d, gi, gj, T)]);
+        if (fin_ring_code<T>(ring, g, li, lj) != (uint32_t)opposite(k)) continue;  // also rejects cells off the grid
+        in = ff_add(in, xval[global_slot(d, g.i0 + li, g.j0 + lj, T)]);
         any = true;
       }
       if (any) {
-        const int c = i * T + j;
-        rcell[atomicAdd(&misc[0], 1)] = (uint16_t)c;
-        F[c] = in;
-        mk[c] = MK_REC;
+        const int r = (int)atomicAdd(&misc[0], 1u);
+        rcell[r] = (uint16_t)(i * T + j);
+        rin[r] = in;
+        if (isfinite(in.hi))
+          atomicMax(&misc[1], (uint32_t)(ebound(in.hi) + 1024));
+        else
+          misc[4] = 1u;
       }
     }
     __syncthreads();
-    const int nrec = misc[0];
-    // marking walk (integer atomics only)
+    const int nrec = (int)misc[0];
+    if (misc[4]) {  // an infinite or NaN inflow
+      if (threadIdx.x == 0) set_status(p.status, D8_ERR_NONFINITE);
+      __syncthreads();  // misc is reset by the next tile
+      continue;
+    }
+    if (nrec == 0) {  // no inflow: A is final
+      __syncthreads();
+      continue;
+    }
+    // S = sum of 2^(e_r - emax + 40), each term rounded up to at least 1
+    const int emax = (int)misc[1] - 1024;
     for (int r = threadIdx.x; r < nrec; r += NTF) {
-      int c = rcell[r];
-      for (int step = 0; step < TT; step++) {
-        const int n = down(c, g);
-        if (n < 0) break;
-        const uint32_t old = atomicAdd(&mk[n], MK_CNT1 | (1u << opposite(code[c])));
-        if (old & (0xFF00u | MK_REC)) break;  // reached before, or a receiver with a walk of its own
-        c = n;
+      const int sh = ebound(rin[r].hi) - emax + 40;
+      atomicAdd(S, sh <= 0 ? 1ull : 1ull << sh);
+    }
+    __syncthreads();
+    // sum |in_r| < S * 2^(emax - 40) <= 2^(ceil(log2 S) + emax - 40)
+    const int q = FxLimbs<T>::VB - 2 - (64 - __clzll(*S - 1ull)) - (emax - 40);
+    // Algorithm 8 on the receivers' paths, in fixed point
+    for (int r = threadIdx.x; r < nrec; r += NTF) {
+      const ff in = rin[r];
+      uint32_t x0, x1, x2;
+      fx_split<T>(fx96_add(fx96_of(in.hi, q), fx96_of(in.lo, q)), x0, x1, x2);
+      int c = rcell[r], i = c / T, j = c & (T - 1);
+      for (int step = 0; step <= TT; step++) {
+        const uint32_t o0 = atomicAdd(F0 + c, x0);
+        const int k = code[c];  // the walk goes on while the reply is in flight
+        const uint32_t up = x1 + ((o0 + x0 < o0) ? 1u : 0u);
+        if (up) atomicAdd(F0 + TT + c, up);
+        if (x2) atomicAdd(F0 + 2 * TT + c, x2);
+        if (k >= 8) break;
+        i += code_di(k);
+        j += code_dj(k);
+        if ((unsigned)i >= (unsigned)g.th || (unsigned)j >= (unsigned)g.tw) break;
+        c = i * T + j;
       }
     }
     __syncthreads();
-    // the receivers with no inflow-carrying input start the propagation; noted
-    // before any walk changes the counts
-    uint32_t starts = 0;
+    // A = fp32(A + F) where F is non-zero; those words go back to zero
 #pragma unroll
-    for (int k = 0; k < RPT; k++) {
-      const int r = threadIdx.x + k * NTF;
-      if (r < nrec && ((mk[rcell[r]] >> 8) & 0xFFu) == 0u) starts |= 1u << k;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) misc[0] = 0;
-#pragma unroll
-    for (int k = 0; k < RPT; k++) {
-      if (!((starts >> k) & 1u)) continue;
-      int c = rcell[threadIdx.x + k * NTF];
-      for (int step = 0; step < TT; step++) {
-        const int n = down(c, g);
-        if (n < 0) break;
-        __threadfence_block();  // F[c] before the arrival that publishes it
-        const uint32_t old = atomicSub(&mk[n], MK_CNT1);
-        if (((old >> 8) & 0xFFu) != 1u) break;
-        __threadfence_block();
-        ff v = F[n];  // its own inflow (receivers) or zero
-        for (uint32_t m = old & 0xFFu; m; m &= m - 1) v = ff_add(v, F[n + toff_tab<T>(__ffs(m) - 1)]);
-        F[n] = v;
-        c = n;
-      }
-    }
-    __syncthreads();
-    // A = fp32(A + F) on the cells inflow reached (float-float add, fp32
-    // arithmetic only: fp64 is slow on this GPU); F and marks go back to zero
-    float4* F4 = reinterpret_cast<float4*>(F);
-    for (int q = threadIdx.x; q < TT / 4; q += NTF) {
-      const uint4 m4 = reinterpret_cast<const uint4*>(mk)[q];
-      if (!(m4.x | m4.y | m4.z | m4.w)) continue;  // F is nonzero only on marked cells
-      reinterpret_cast<uint4*>(mk)[q] = make_uint4(0, 0, 0, 0);
-      const float4 fa = F4[2 * q], fb = F4[2 * q + 1];  // {hi, lo} of four cells
-      F4[2 * q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      F4[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const int c = q * 4, i = c / T, j = c - i * T;
+    for (int rr = 0; rr < NQ; rr++) {
+      const int qd = threadIdx.x + rr * NTF;
+      const uint4 a4 = reinterpret_cast<const uint4*>(F0)[qd];
+      const uint4 b4 = reinterpret_cast<const uint4*>(F0 + TT)[qd];
+      const uint4 c4 = reinterpret_cast<const uint4*>(F0 + 2 * TT)[qd];
+      if (!(a4.x | a4.y | a4.z | a4.w | b4.x | b4.y | b4.z | b4.w | c4.x | c4.y | c4.z | c4.w)) continue;
+      reinterpret_cast<uint4*>(F0)[qd] = make_uint4(0, 0, 0, 0);
+      reinterpret_cast<uint4*>(F0 + TT)[qd] = make_uint4(0, 0, 0, 0);
+      reinterpret_cast<uint4*>(F0 + 2 * TT)[qd] = make_uint4(0, 0, 0, 0);
+      const int c = qd * 4, i = c / T, j = c - i * T;
       if (i >= g.th) continue;
-      const ff f[4] = {ff{fa.x, fa.y}, ff{fa.z, fa.w}, ff{fb.x, fb.y}, ff{fb.z, fb.w}};
-      const bool on[4] = {(m4.x & 0x1FFFFu) != 0u, (m4.y & 0x1FFFFu) != 0u, (m4.z & 0x1FFFFu) != 0u,
-                          (m4.w & 0x1FFFFu) != 0u};
+      const uint32_t w0[4] = {a4.x, a4.y, a4.z, a4.w}, w1[4] = {b4.x, b4.y, b4.z, b4.w},
+                     w2[4] = {c4.x, c4.y, c4.z, c4.w};
+      ff f[4];
+      bool on[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const fx96 v = fx_join<T>(w0[k], w1[k], w2[k]);
+        on[k] = (v.w0 | v.w1 | v.w2) != 0u;
+        f[k] = fx96_to_ff(v.w0, v.w1, v.w2, q);
+      }
       float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
       if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
         float4 a = *reinterpret_cast<float4*>(dst);

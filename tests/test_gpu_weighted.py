@@ -178,3 +178,22 @@ def test_backward_reports_cycles(d8, T):
         np.testing.assert_array_equal(g, oracle.transposed(ok, np.ones((96, 150))).astype(np.float32))
     finally:
         d8.set_tile(64)
+
+
+def test_weighted_wide_dynamic_range(d8):
+    """Weights spanning eleven orders of magnitude: a band of huge weights
+    upstream sends rivers of ~1e9 through tiles whose other receivers carry
+    inflows near 1e-2.  The per-tile fixed-point finalise must keep those
+    small inflows within the bar (its scale follows the tile's summed
+    inflow, not only the largest)."""
+    H, W = 1200, 1100
+    z = demgen.fractal(H, W, seed=41, cache=False)
+    d_ref = oracle.flowdir(z)
+    w = demgen.lognormal_weights(H, W, seed=13) * np.float32(1e-2)
+    hi = z > np.quantile(z, 0.9)  # the highest tenth of the DEM
+    w[hi] *= np.float32(1e9)
+    A = d8.accumulate_weighted(to_dev(d_ref), to_dev(w)).cpu().numpy()
+    A64 = oracle.accumulate_weighted(d_ref, w.astype(np.float64))
+    assert A64.max() / A64.min() > 1e10
+    assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
+    assert d8.get_status() == "OK"
