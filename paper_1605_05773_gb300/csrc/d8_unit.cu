@@ -38,8 +38,8 @@ namespace unit {
 
 constexpr int NTU = 128;  // threads per tile block (4 warps)
 constexpr int NTW = 256;  // threads per weighted tile block of side 64 and up (8 warps)
-// Threads per tile of the first pass: a weighted 64 x 64 tile needs 57 KB of
-// shared memory (3 per SM), so weighted tiles of 64 and up get 8 warps each
+// Threads per tile of the first pass: a weighted 64 x 64 tile needs 49 KB of
+// shared memory (4 per SM), so weighted tiles of 64 and up get 8 warps each
 // to keep enough warps resident; 32 x 32 tiles have too few cells for that.
 template <int T, bool WT>
 struct UpThreads {
@@ -143,8 +143,8 @@ template <int T, bool WT>
 struct UpLayout {
   static constexpr size_t TT = (size_t)T * T;
   static constexpr size_t off_word = 0;
-  static constexpr size_t off_seg = TT * 4;
-  static constexpr size_t off_ring = off_seg + TT * 2;  // one ring of RING entries per warp
+  static constexpr size_t off_seg = TT * 4;             // unit counts only (weighted tiles chase next pointers)
+  static constexpr size_t off_ring = off_seg + (WT ? 0 : TT * 2);  // one ring of RING entries per warp
   static constexpr size_t off_misc = off_ring + (size_t)(UpThreads<T, WT>::N / 32) * RING * 2;
   static constexpr size_t off_val = off_misc + 64;  // weighted: float-float value per cell
   static constexpr size_t bytes = off_val + (WT ? TT * sizeof(ff) : 0);
@@ -301,6 +301,15 @@ __device__ __forceinline__ void perimeter_summary(const TileGeo& g, int64_t t, c
         pv = W::cnt(w);
       if (w & W_EXIT) {
         pe = (uint16_t)(PEX_EXIT | W::code(w));
+      } else if (WT && (w & W_IN) && !cyc) {
+        // weighted tiles keep no segment records: follow the next pointers
+        int e = c;
+        uint32_t we = w;
+        for (int guard = 0; (we & W_IN) && guard < TT; guard++) {
+          e = W::next(we, e);
+          we = word[e];
+        }
+        if (we & W_EXIT) pe = (uint16_t)slot_of(e / T, e % T, g.th, g.tw, T);
       } else if ((w & W_IN) && !cyc) {
         volatile uint16_t* vs = seg;
         const uint16_t v = vs[c];
@@ -329,7 +338,7 @@ __device__ __forceinline__ void perimeter_summary(const TileGeo& g, int64_t t, c
 }
 
 template <int T, bool WT>
-__global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(DemTable dt, Pipe p) {
+__global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 4 : 8) k_up_unit(DemTable dt, Pipe p) {
   constexpr int NT = UpThreads<T, WT>::N;
   using L = UpLayout<T, WT>;
   using W = WL<T>;
@@ -408,7 +417,7 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(Dem
             const int s = W::next(wv, cur);
             const uint32_t old = atomicAdd(&word[s], WT ? 0u - W_LEFT1 : acc - W_LEFT1);
             if (W::last(old)) {  // last input to arrive: continue there
-              seg[s] = (uint16_t)h;
+              if (!WT) seg[s] = (uint16_t)h;
               if (WT) {
                 __threadfence_block();
                 v = pull_value<T>(val, s, old);
@@ -419,11 +428,11 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 3 : 8) k_up_unit(Dem
               cur = s;
               done++;
             } else {
-              seg[h] = (uint16_t)(SEG_REC | s);
+              if (!WT) seg[h] = (uint16_t)(SEG_REC | s);
               cur = -1;
             }
           } else {
-            seg[h] = (uint16_t)(SEG_REC | SEG_END | cur);
+            if (!WT) seg[h] = (uint16_t)(SEG_REC | SEG_END | cur);
             cur = -1;
           }
         }
