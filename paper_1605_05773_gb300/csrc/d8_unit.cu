@@ -77,6 +77,9 @@ constexpr uint32_t W_IN = 1u << 25, W_EXIT = 1u << 26, W_LEFT1 = 1u << 28;
 // are in-tile inputs (bit k: the input lies in direction k) and bit 27 marks a
 // cell present in the tile.  A source has no input and nothing left.
 constexpr uint32_t W_PRES = 1u << 27, W_SRC_W = 0xF0000000u | W_PRES | 0xFFu;
+// Unit words use bit 27 to mark a cell whose inputs were all delivered by the
+// source sweep (the cell then starts a walk).
+constexpr uint32_t W_READY = 1u << 27;
 template <int T>
 struct WL {
   static constexpr bool IDX = T <= 64;
@@ -362,18 +365,44 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 4 : 8) k_up_unit(Dem
     __syncthreads();
     tile_codes_from_dir<T, WT>(d, g, word, val, p.status);  // Algorithm 1
     __syncthreads();
-    // Algorithm 2.  Every lane walks down-slope from a source while it is the
-    // last input to arrive at the next cell; a lane whose walk stopped takes
-    // the warp's next pending source.  Pending sources sit in a per-warp ring,
-    // refilled by scanning the warp's own cells (c = lane + 32 w + NT r) a
-    // row at a time with a ballot.  A source is a cell with count 1 and no
-    // input left (an absent cell of a ragged tile has count 0); the word of a
-    // cell whose last input has arrived holds count >= 2, so a scan running
-    // behind the walks never takes it for one.  Weighted tiles carry values
-    // instead of counts: a finished cell stores its value before the atomic
-    // that publishes its arrival (block fence between), and the last arriver
-    // pulls its inputs' values after it (fence again).
     int done = 0;
+    if (!WT) {
+      // Source sweep (unit counts).  A source (count 1, no input) would start
+      // a walk whose first step delivers its 1 to its target; on terrain two
+      // cells in five are sources and most such walks end after that step.
+      // So every source delivers in one data-parallel pass instead, and the
+      // source that delivers a target's last input marks the target READY:
+      // walks start only at READY cells (one cell in seven), carrying their
+      // count.  A swept source's segment record says its one-step walk stopped
+      // before its target (or ended at the source itself).
+#pragma unroll 4
+      for (int r = 0; r < TT / NT; r++) {
+        const int c = threadIdx.x + r * NT;
+        const uint32_t w = word[c];
+        if ((w & W::SRC_MASK) != 1u) continue;
+        done++;
+        if (w & W_IN) {
+          const int s = W::next(w, c);
+          const uint32_t old = atomicAdd(&word[s], 1u - W_LEFT1);
+          seg[c] = (uint16_t)(SEG_REC | s);
+          if (W::last(old)) atomicOr(&word[s], W_READY);
+        } else {
+          seg[c] = (uint16_t)(SEG_REC | SEG_END | c);
+        }
+      }
+      __syncthreads();
+    }
+    // Algorithm 2.  Every lane walks down-slope from a start cell while it is
+    // the last input to arrive at the next cell; a lane whose walk stopped
+    // takes the warp's next pending start.  Pending starts sit in a per-warp
+    // ring, refilled by scanning the warp's own cells (c = lane + 32 w + NT r)
+    // a row at a time with a ballot.  Unit counts start at READY cells (a
+    // cell reached by a walk's last arrival never carries the mark, so a scan
+    // running behind the walks never takes it).  Weighted tiles start at
+    // sources (no input left, present) and carry values instead of counts: a
+    // finished cell stores its value before the atomic that publishes its
+    // arrival (block fence between), and the last arriver pulls its inputs'
+    // values after it (fence again).
     {
       int r = 0, head = 0, tail = 0, cur = -1, h = 0;
       uint32_t acc = 0, wv = 0;
@@ -381,7 +410,7 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 4 : 8) k_up_unit(Dem
       for (;;) {
         while (tail - head < 32 && r < TT / NT) {  // at most RING - 1 pending
           const int c = threadIdx.x + r * NT;
-          const bool src = WT ? (word[c] & W_SRC_W) == W_PRES : (word[c] & W::SRC_MASK) == 1u;
+          const bool src = WT ? (word[c] & W_SRC_W) == W_PRES : (word[c] & W_READY) != 0u;
           const unsigned m = __ballot_sync(FULL, src);
           if (src) ring[(tail + __popc(m & lt)) & (RING - 1)] = (uint16_t)c;
           tail += __popc(m);
@@ -395,7 +424,7 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 4 : 8) k_up_unit(Dem
             cur = ring[idx & (RING - 1)];
             h = cur;
             wv = word[cur];
-            acc = 1;  // a source
+            acc = WT ? 1u : W::cnt(wv);  // a READY cell's count (unit) / a source
             if (WT) v = val[cur];  // its weight
             done++;
           }
