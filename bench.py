@@ -637,14 +637,19 @@ def run_ours(args, world, rank, local):
             "cpu_reference_mt": mt,
             "clocks": clk,
         }
-        if world == 1 and not args.no_extras:
+        extras = set() if args.no_extras else set(args.extras.split(",")) - {""}
+        if world == 1 and extras:
             lib.set_profiling(False, dev)
-            line["batched"] = run_batched(dev, stream, max(3, min(args.steps, 5)))
-            lib.set_tile(args.tile)
-            lib.set_strategy(args.strategy)
-            line["fwd_bwd"] = run_fwd_bwd(dev, stream, max(3, min(args.steps, 10)))
-            line["workloads"] = run_workloads(dev, stream, max(3, min(args.steps, 10)))
-            line["fill"] = run_fill(dev, 3)
+            if "batched" in extras:
+                line["batched"] = run_batched(dev, stream, max(3, min(args.steps, 5)))
+                lib.set_tile(args.tile)
+                lib.set_strategy(args.strategy)
+            if "fwd_bwd" in extras:
+                line["fwd_bwd"] = run_fwd_bwd(dev, stream, max(3, min(args.steps, 10)))
+            if "workloads" in extras:
+                line["workloads"] = run_workloads(dev, stream, max(3, min(args.steps, 10)))
+            if "fill" in extras:
+                line["fill"] = run_fill(dev, 3)
         print(json.dumps(line), flush=True)
     return 0
 
@@ -659,8 +664,13 @@ def main():
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--strategy", choices=["ring", "lane_mask", "jump"], default="ring")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched, fwd+bwd and workloads lines")
+    ap.add_argument("--extras", default="batched,fwd_bwd,workloads,fill",
+                    help="comma-separated extra lines to add (batched, fwd_bwd, workloads, fill)")
+    ap.add_argument("--no-extras", action="store_true", help="add none of the extra lines")
     args = ap.parse_args()
+    bad = set(args.extras.split(",")) - {"", "batched", "fwd_bwd", "workloads", "fill"}
+    if bad:
+        ap.error(f"unknown extras: {sorted(bad)}")
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         rc = run_reference(args, world, rank)

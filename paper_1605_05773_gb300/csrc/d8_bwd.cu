@@ -244,10 +244,13 @@ __global__ void k_bpj_init(DemTable dt, Pipe p) {
 // parent <- parent(parent), written to the other buffers.  An exit whose
 // parent became ROOT is listed once more, for a round that only copies its
 // final H into the other buffer, so that both buffers end up final for every
-// slot (a later round may gather it from either).  The grid-stride loop runs
-// the same number of times in every lane of a warp (the stride is a multiple
-// of 32), as warp_append requires.
-__global__ void k_bpj_round(Pipe p, int r) {
+// slot (a later round may gather it from either).  Each thread takes BPJ_U
+// list items per pass and issues all their loads before using any (the
+// gathers are dependent pairs of random loads).  The pass loop runs the same
+// number of times in every lane of a warp (the stride is a multiple of 32),
+// as warp_append requires.
+constexpr int BPJ_U = 4;
+__global__ void __launch_bounds__(256) k_bpj_round(Pipe p, int r) {
   const uint32_t n = *(volatile uint32_t*)&p.flags[r];
   if (n == 0u) return;
   const ff* Hc = static_cast<const ff*>((r & 1) ? p.S2 : p.S);
@@ -257,25 +260,46 @@ __global__ void k_bpj_round(Pipe p, int r) {
   const uint32_t* lc = p.list[r & 1];
   uint32_t* ln = p.list[(r + 1) & 1];
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < (int64_t)n; base += stride) {
-    const int64_t i = base + lane;
-    bool keep = false;
-    uint32_t g = 0;
-    if (i < (int64_t)n) {
-      g = lc[i];
-      const uint32_t par = Pc[g];
-      ff h = Hc[g];
-      uint32_t pp = ROOT;
-      if (par != ROOT) {
-        h = ff_add(h, Hc[par]);
-        pp = Pc[par];
-        keep = true;
-      }
-      Hn[g] = h;
-      Pn[g] = pp;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < (int64_t)n; base += BPJ_U * nt) {
+    uint32_t g[BPJ_U], par[BPJ_U], pp[BPJ_U];
+    ff h[BPJ_U], hp[BPJ_U];
+    bool ok[BPJ_U];
+#pragma unroll
+    for (int u = 0; u < BPJ_U; u++) {
+      const int64_t i = base + lane + u * nt;
+      ok[u] = i < (int64_t)n;
+      g[u] = ok[u] ? lc[i] : 0u;
     }
-    warp_append(keep, g, ln, &p.flags[r + 1]);
+#pragma unroll
+    for (int u = 0; u < BPJ_U; u++) {
+      par[u] = ROOT;
+      if (ok[u]) {
+        par[u] = Pc[g[u]];
+        h[u] = Hc[g[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BPJ_U; u++) {
+      pp[u] = ROOT;
+      if (ok[u] && par[u] != ROOT) {
+        hp[u] = Hc[par[u]];
+        pp[u] = Pc[par[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BPJ_U; u++) {
+      bool keep = false;
+      if (ok[u]) {
+        if (par[u] != ROOT) {
+          h[u] = ff_add(h[u], hp[u]);
+          keep = true;
+        }
+        Hn[g[u]] = h[u];
+        Pn[g[u]] = pp[u];
+      }
+      warp_append(keep, g[u], ln, &p.flags[r + 1]);
+    }
   }
 }
 
@@ -398,7 +422,7 @@ static cudaError_t launch_combine_bwd_t(const DemTable& dt, const Pipe& p, cudaS
   if (e != cudaSuccess) return e;
   k_bpj_init<T><<<grid_for_b(p.nslots, 16), 256, 0, s>>>(dt, p);
   ++*nlaunch;
-  const unsigned gr = grid_for_b(p.nslots, 8);
+  const unsigned gr = grid_for_b((p.nslots + BPJ_U - 1) / BPJ_U, 4);
   for (int r = 0; r < R; r++) {
     k_bpj_round<<<gr, 256, 0, s>>>(p, r);
     ++*nlaunch;
