@@ -177,8 +177,8 @@ __device__ int group_load(const DemDesc& cd, int64_t gy, int64_t gx, const uint1
 // Algorithm 2 on the exit forest of a group: last-arriver walks from the
 // nodes without unfinished children.  A finished node adds its value to its
 // parent, then (after a block fence) decrements the parent's children count;
-// the last child continues at the parent (after a fence, so it sees every
-// child's addition).  Returns the number of nodes this thread finished.
+// the last child continues at the parent (its acquire-release count atomic
+// orders it after every child's addition).  Returns the number of nodes this thread finished.
 template <int S, int G, class V>
 __device__ int group_walk(uint16_t* spx, V* val, uint32_t* pd, uint16_t* srcl) {
   constexpr int NS = G * G * 4 * S;
@@ -217,10 +217,10 @@ __device__ int group_walk(uint16_t* spx, V* val, uint32_t* pd, uint16_t* srcl) {
         continue;
       }
       vatomic_add(&val[p], v);
-      __threadfence_block();
-      const uint32_t old = atomicSub(&pd[p], 1u);
+      // the addition above is released by the count's atomic; the last child
+      // reads the parent's value after it (acquire)
+      const uint32_t old = atomic_add_acq_rel_cta(&pd[p], 0u - 1u);
       if (pd_deg(old) == 1u) {
-        __threadfence_block();
         cur = p;
         v = vload_volatile(&val[p]);
         done++;
@@ -489,9 +489,7 @@ __global__ void k_top_walk(const uint32_t* par, V* fin, uint32_t* deg, const uin
         const uint32_t p = par[x];
         if (p == ROOT) break;
         vatomic_add(&fin[p], v);
-        __threadfence();
-        if (atomicSub(&deg[p], 1u) != 1u) break;
-        __threadfence();
+        if (atomic_add_acq_rel_gpu(&deg[p], 0u - 1u) != 1u) break;  // releases the addition; acquires the others'
         x = p;
         v = vload_volatile(&fin[p]);
         done++;

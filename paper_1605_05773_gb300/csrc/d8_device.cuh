@@ -75,6 +75,26 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, int nbytes
                "l"(src), "r"(nbytes)
                : "memory");
 }
+// Shared-memory atomic add with acquire-release semantics at CTA scope: the
+// writes this thread made before it are visible to any thread whose later
+// acquire atomic on the same word reads its result (or a later one), and the
+// reads this thread makes after it see what those earlier releasers wrote.
+__device__ __forceinline__ uint32_t atomic_add_acq_rel_cta(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;\n"
+               : "=r"(old)
+               : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v)
+               : "memory");
+  return old;
+}
+
+// The same in global memory at GPU scope.
+__device__ __forceinline__ uint32_t atomic_add_acq_rel_gpu(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;\n" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {

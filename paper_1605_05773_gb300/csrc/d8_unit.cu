@@ -438,17 +438,15 @@ __global__ void __launch_bounds__(UpThreads<T, WT>::N, WT ? 4 : 8) k_up_unit(Dem
 #pragma unroll
         for (int k = 0; k < (WT ? 2 : UNIT_STEPS); k++) {
           if (cur < 0) break;
-          if (WT) {
-            val[cur] = v;
-            __threadfence_block();
-          }
+          if (WT) val[cur] = v;
           if (wv & W_IN) {
             const int s = W::next(wv, cur);
-            const uint32_t old = atomicAdd(&word[s], WT ? 0u - W_LEFT1 : acc - W_LEFT1);
+            // weighted: the value store above is released by the atomic, and
+            // the last arriver's pull below is ordered after it (acquire)
+            const uint32_t old = WT ? atomic_add_acq_rel_cta(&word[s], 0u - W_LEFT1) : atomicAdd(&word[s], acc - W_LEFT1);
             if (W::last(old)) {  // last input to arrive: continue there
               if (!WT) seg[s] = (uint16_t)h;
               if (WT) {
-                __threadfence_block();
                 v = pull_value<T>(val, s, old);
               } else {
                 acc += W::cnt(old);
