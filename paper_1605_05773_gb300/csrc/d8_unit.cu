@@ -860,11 +860,16 @@ __device__ __forceinline__ fx96 fx_join(uint32_t w0, uint32_t w1, uint32_t w2) {
   return fx96_add(a, b);
 }
 
+// 2^k as fp32 for -126 <= k <= 127 (built from its exponent field: exact)
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
 // The fixed-point value (w0, w1, w2) * 2^-q as float-float: the top 62 bits
 // of the magnitude rounded to fp32, plus their exact remainder rounded to
 // fp32 (a relative error of at most 2^-48 from the remainder's rounding and
-// 2^-61 from the bits below the top 62).
-__device__ __forceinline__ ff fx96_to_ff(uint32_t w0, uint32_t w1, uint32_t w2, int q) {
+// 2^-61 from the bits below the top 62).  2^-q is passed as two powers of two
+// p1 * p2 of the normal range; each product below is exact until the last,
+// which rounds once.
+__device__ __forceinline__ ff fx96_to_ff(uint32_t w0, uint32_t w1, uint32_t w2, float p1, float p2) {
   uint64_t lo = w0 | ((uint64_t)w1 << 32);
   uint32_t hi = w2;
   const bool neg = (hi >> 31) != 0u;
@@ -881,7 +886,8 @@ __device__ __forceinline__ ff fx96_to_ff(uint32_t w0, uint32_t w1, uint32_t w2, 
   }
   const float fh = __ull2float_rn(U);  // U < 2^62 rounded to 24 bits: an integer
   const float fl = __ll2float_rn((long long)(U - __float2ull_rn(fh)));
-  const ff r{ldexpf(fh, sh - q), ldexpf(fl, sh - q)};
+  const float sc = pow2f(sh);  // sh <= 34
+  const ff r{__fmul_rn(__fmul_rn(__fmul_rn(fh, sc), p1), p2), __fmul_rn(__fmul_rn(__fmul_rn(fl, sc), p1), p2)};
   return neg ? ff{-r.hi, -r.lo} : r;
 }
 
@@ -979,6 +985,8 @@ __global__ void __launch_bounds__(NTF, T >= 64 ? 4 : 8) k_fin_w(DemTable dt, Pip
     __syncthreads();
     // sum |in_r| < S * 2^(emax - 40) <= 2^(ceil(log2 S) + emax - 40)
     const int q = FxLimbs<T>::VB - 2 - (64 - __clzll(*S - 1ull)) - (emax - 40);
+    // 2^-q as two powers of two of the normal range (|q| <= 250: -126 <= emax <= 128)
+    const float p1 = pow2f(-q / 2), p2 = pow2f(-q - (-q / 2));
     // Algorithm 8 on the receivers' paths, in fixed point
     for (int r = threadIdx.x; r < nrec; r += NTF) {
       const ff in = rin[r];
@@ -1020,7 +1028,7 @@ __global__ void __launch_bounds__(NTF, T >= 64 ? 4 : 8) k_fin_w(DemTable dt, Pip
       for (int k = 0; k < 4; k++) {
         const fx96 v = fx_join<T>(w0[k], w1[k], w2[k]);
         on[k] = (v.w0 | v.w1 | v.w2) != 0u;
-        f[k] = fx96_to_ff(v.w0, v.w1, v.w2, q);
+        f[k] = on[k] ? fx96_to_ff(v.w0, v.w1, v.w2, p1, p2) : ff{0.0f, 0.0f};
       }
       float* dst = static_cast<float*>(d.A) + (g.i0 + i) * d.ldA + (g.j0 + j);
       if (g.tw == T && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {

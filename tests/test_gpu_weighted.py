@@ -197,3 +197,23 @@ def test_weighted_wide_dynamic_range(d8):
     assert A64.max() / A64.min() > 1e10
     assert (np.abs(A - A64) / np.abs(A64)).max() <= TOL
     assert d8.get_status() == "OK"
+
+
+@pytest.mark.parametrize("T", [32, 64])
+def test_weighted_signed_weights(d8, T):
+    """Weights of both signs (N(0, 1)), so inflows cancel along the paths and
+    the finalise's fixed point carries negative values and borrows.  Error
+    is measured against the scale of the terms, |A32 - A64| / (sum of |w|
+    over the up-slope set), the reading used for signed gradients."""
+    d8.set_tile(T)
+    try:
+        H, W = 1100, 1300
+        d_ref = oracle.flowdir(demgen.fractal(H, W, seed=43, cache=False))
+        w = demgen.normal_cotangent(H, W, seed=15)
+        A = d8.accumulate_weighted(to_dev(d_ref), to_dev(w)).cpu().numpy()
+        A64 = oracle.accumulate_weighted(d_ref, w.astype(np.float64))
+        scale = oracle.accumulate_weighted(d_ref, np.abs(w).astype(np.float64))
+        assert (np.abs(A.astype(np.float64) - A64) / scale).max() <= TOL
+        assert d8.get_status() == "OK"
+    finally:
+        d8.set_tile(64)
