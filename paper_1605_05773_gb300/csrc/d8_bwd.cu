@@ -311,25 +311,29 @@ __global__ void k_bpj_check(Pipe p, int R) {
 // dw(q) = (in-tile path sum of q, already in dw) + H(exit of q); four
 // consecutive cells of a row per thread (8-byte exit-slot loads, 16-byte dw
 // accesses) when the row layout allows, else one cell per thread
-template <int T, bool VEC>
+template <int T, int V>
 __global__ void k_bwd_fix(DemTable dt, Pipe p) {
   const DemDesc d = dt.one;
   const ff* H = static_cast<const ff*>(p.S);  // final in both buffers
-  constexpr int V = VEC ? 4 : 1;
   const int64_t wq = d.W / V;  // groups per row
   const int64_t n = d.H * wq;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
     const int64_t gi = k / wq, gj = (k - gi * wq) * V;
     uint16_t e[V];
-    if (VEC) {
-      const uint2 e4 = *reinterpret_cast<const uint2*>(p.xid + gi * d.W + gj);
-      e[0] = (uint16_t)e4.x;
-      e[V > 1 ? 1 : 0] = (uint16_t)(e4.x >> 16);
-      e[V > 2 ? 2 : 0] = (uint16_t)e4.y;
-      e[V > 3 ? 3 : 0] = (uint16_t)(e4.y >> 16);
+    const uint16_t* xp = p.xid + gi * d.W + gj;
+    if constexpr (V == 8) {
+      const uint4 x = *reinterpret_cast<const uint4*>(xp);
+      const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int u = 0; u < V; u++) e[u] = (uint16_t)(xw[(u / 2) & 3] >> (16 * (u & 1)));
+    } else if constexpr (V == 4) {
+      const uint2 x = *reinterpret_cast<const uint2*>(xp);
+      const uint32_t xw[2] = {x.x, x.y};
+#pragma unroll
+      for (int u = 0; u < V; u++) e[u] = (uint16_t)(xw[(u / 2) & 1] >> (16 * (u & 1)));
     } else {
-      e[0] = p.xid[gi * d.W + gj];
+      e[0] = xp[0];
     }
     bool any = false;
 #pragma unroll
@@ -337,16 +341,19 @@ __global__ void k_bwd_fix(DemTable dt, Pipe p) {
     if (!any) continue;
     float* dst = static_cast<float*>(d.A) + gi * d.ldA + gj;
     const int64_t trow = (gi / T) * d.ntx;
-    if (VEC) {
-      float4 a = *reinterpret_cast<float4*>(dst);
-      float* av = reinterpret_cast<float*>(&a);
+    if constexpr (V >= 4) {
+      float4 a[V / 4];
+#pragma unroll
+      for (int h = 0; h < V / 4; h++) a[h] = reinterpret_cast<const float4*>(dst)[h];
+      float* av = reinterpret_cast<float*>(a);
 #pragma unroll
       for (int u = 0; u < V; u++) {
         if (e[u] == NO_EXIT) continue;
         const ff v = ff_add(ff{av[u], 0.0f}, H[(trow + (gj + u) / T) * (4 * T) + e[u]]);
         av[u] = __fadd_rn(v.hi, v.lo);
       }
-      *reinterpret_cast<float4*>(dst) = a;
+#pragma unroll
+      for (int h = 0; h < V / 4; h++) reinterpret_cast<float4*>(dst)[h] = a[h];
     } else {
       const ff v = ff_add(ff{*dst, 0.0f}, H[(trow + gj / T) * (4 * T) + e[0]]);
       *dst = __fadd_rn(v.hi, v.lo);
@@ -391,13 +398,18 @@ static cudaError_t launch_bwd_up_t(const DemTable& dt, const Pipe& p, cudaStream
 
 template <int T>
 static cudaError_t launch_bwd_fix_t(const DemTable& dt, const Pipe& p, cudaStream_t s) {
+  // eight or four cells per thread (16- or 8-byte exit-slot loads, 16-byte
+  // dw accesses) when every row start stays aligned, else one
   const DemDesc& d = dt.one;
-  const bool vec = d.W % 4 == 0 && d.ldA % 4 == 0 && (reinterpret_cast<uintptr_t>(d.A) & 15u) == 0;
-  const unsigned b = grid_for_b(d.H * (vec ? d.W / 4 : d.W), 32);
-  if (vec)
-    k_bwd_fix<T, true><<<b, 256, 0, s>>>(dt, p);
+  const bool a16 = (reinterpret_cast<uintptr_t>(d.A) & 15u) == 0;
+  const int v = (a16 && d.W % 8 == 0 && d.ldA % 8 == 0) ? 8 : (a16 && d.W % 4 == 0 && d.ldA % 4 == 0) ? 4 : 1;
+  const unsigned b = grid_for_b(d.H * (d.W / v), 32);
+  if (v == 8)
+    k_bwd_fix<T, 8><<<b, 256, 0, s>>>(dt, p);
+  else if (v == 4)
+    k_bwd_fix<T, 4><<<b, 256, 0, s>>>(dt, p);
   else
-    k_bwd_fix<T, false><<<b, 256, 0, s>>>(dt, p);
+    k_bwd_fix<T, 1><<<b, 256, 0, s>>>(dt, p);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ def grad_error(g32, d_ref, c):
 
 
 @pytest.mark.parametrize("T", [32, 64, 128])
-@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (97, 131), (300, 257), (520, 130)])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (97, 131), (300, 257), (520, 130), (131, 300), (64, 1024)])
 def test_weighted_and_backward_small(d8, T, shape):
     d8.set_tile(T)
     try:
