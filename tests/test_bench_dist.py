@@ -93,3 +93,14 @@ def test_measured_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypa
 
 if __name__ == "__main__":
     sys.exit(pytest.main([__file__, "-q"]))
+
+
+def test_unknown_extras_are_refused():
+    """bench.py --extras names the extra lines to add; a misspelt name is an
+    argument error (before any GPU work), not a silently skipped line."""
+    import subprocess
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--extras", "fwd_bwd,fil"],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2
+    assert "unknown extras" in r.stderr and "fil" in r.stderr
