@@ -14,9 +14,10 @@
 // GPU layout: 64 x 64 tiles.  A round visits the tiles marked active: a
 // thread block loads the tile's z and the current F of the tile and its
 // one-cell halo into shared memory and relaxes the tile to a local fixed
-// point in waves (a wave updates the cells marked dirty; a cell whose value
-// drops marks its neighbours dirty for the next wave), then writes the tile
-// back.  A tile whose border values dropped marks its eight neighbouring
+// point, first in waves (a wave updates the cells marked dirty; a cell whose
+// value drops marks its neighbours dirty for the next wave), then, if a few
+// waves do not settle it, in directional sweeps along rows and columns; then
+// it writes the tile back.  A tile whose border values dropped marks its eight neighbouring
 // tiles active for the next round.  A round in which no tile marks any
 // other ends the fill: every tile is then at a fixed point of its final halo,
 // so F is the global fixed point.
@@ -31,7 +32,8 @@ namespace fill {
 constexpr int T = 64;
 constexpr int NTF = 256;
 constexpr int HW = T + 2;               // halo row width
-constexpr int MAX_WAVES = 4 * T * T;    // then the tile simply stays active
+constexpr int SWEEP_AFTER = 8;          // waves before the tile switches to directional sweeps
+constexpr int MAX_SWEEPS = 4 * T;       // sweep passes (four directions each) before giving up
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
@@ -58,6 +60,21 @@ __global__ void k_fill_init(const float* z, int64_t H, int64_t W, int64_t ldz, f
     F[i * ldF + j] = edge ? zc : INFINITY;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, D8_ERR_NONFINITE);
+}
+
+// Relax tile cell (i, j) once: F(c) = z(c) if z(c) > m else up(m), m the lowest
+// of its eight neighbours' current values; returns whether F(c) dropped.
+__device__ __forceinline__ bool relax_cell(float* Fh, const float* zt, int i, int j, float eps) {
+  float* fc = &Fh[(i + 1) * HW + (j + 1)];
+  const float m = fminf(fminf(fminf(fc[-HW - 1], fc[-HW]), fminf(fc[-HW + 1], fc[-1])),
+                        fminf(fminf(fc[1], fc[HW - 1]), fminf(fc[HW], fc[HW + 1])));
+  const float zc = zt[i * T + j];
+  const float v = zc > m ? zc : up(m, eps);
+  if (v < *fc) {
+    *fc = v;
+    return true;
+  }
+  return false;
 }
 
 // One round over the active tiles.  act_cur / act_next: one byte per tile;
@@ -111,9 +128,9 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
       mk0[MW + q] = 0u;
     }
     __syncthreads();
-    bool tile_changed = false, border_changed = false;
+    bool tile_changed = false, border_changed = false, settled_now = false;
     int wave = 0;
-    for (; wave < MAX_WAVES; wave++) {
+    for (; wave < SWEEP_AFTER; wave++) {
       uint32_t* cur = mk0 + (wave & 1) * MW;
       uint32_t* nxt = mk0 + ((wave + 1) & 1) * MW;
       bool changed = false;
@@ -124,13 +141,7 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
           const int b = __ffs(bits) - 1;
           bits &= bits - 1;
           const int c = q * 16 + b, i = c / T, j = c % T;
-          float* fc = &Fh[(i + 1) * HW + (j + 1)];
-          float m = fminf(fminf(fminf(fc[-HW - 1], fc[-HW]), fminf(fc[-HW + 1], fc[-1])),
-                          fminf(fminf(fc[1], fc[HW - 1]), fminf(fc[HW], fc[HW + 1])));
-          const float zc = zt[c];
-          const float v = zc > m ? zc : up(m, eps);
-          if (v < *fc) {
-            *fc = v;
+          if (relax_cell(Fh, zt, i, j, eps)) {
             changed = true;
             if (i == 0 || j == 0 || i == th - 1 || j == tw - 1) border_changed = true;
 #pragma unroll
@@ -149,7 +160,63 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
       const bool any = __syncthreads_or(changed);
       for (int q = threadIdx.x; q < MW; q += NTF) cur[q] = 0u;
       __syncthreads();
-      if (!any) break;
+      if (!any) {
+        settled_now = true;
+        break;
+      }
+    }
+    if (!settled_now) {
+      // Still changing after SWEEP_AFTER waves: a wave moves a change one cell
+      // per pass, so values that must cross the tile (a depression filling
+      // from its pour point) switch to directional sweeps, each carrying a
+      // change along a whole row or column in one pass: thread r walks row r
+      // left to right, then right to left, then thread r walks column r down
+      // and up.  Any order of updates reaches the same fixed point (the
+      // update is monotone and its fixed point unique), so the result does
+      // not depend on the mix of waves and sweeps.
+      const int r = threadIdx.x;
+      const bool rin = r < th && i0 + r > 0 && i0 + r < H - 1;  // row r holds interior cells
+      const bool cin = r < tw && j0 + r > 0 && j0 + r < W - 1;  // column r holds interior cells
+      const int jlo = j0 == 0 ? 1 : 0, jhi = (int)min64(tw, W - 1 - j0);  // interior columns [jlo, jhi)
+      const int ilo = i0 == 0 ? 1 : 0, ihi = (int)min64(th, H - 1 - i0);  // interior rows [ilo, ihi)
+      // a row pass changes a border cell at its first or last column, or on
+      // the tile's first or last row; a column pass likewise
+      const bool redge = r == 0 || r == th - 1, cedge = r == 0 || r == tw - 1;
+      for (int sw = 0; sw < MAX_SWEEPS; sw++) {
+        bool changed = false;
+        if (rin)
+          for (int j = jlo; j < jhi; j++)
+            if (relax_cell(Fh, zt, r, j, eps)) {
+              changed = true;
+              border_changed |= redge || j == 0 || j == tw - 1;
+            }
+        __syncthreads();
+        if (rin)
+          for (int j = jhi - 1; j >= jlo; j--)
+            if (relax_cell(Fh, zt, r, j, eps)) {
+              changed = true;
+              border_changed |= redge || j == 0 || j == tw - 1;
+            }
+        __syncthreads();
+        if (cin)
+          for (int i = ilo; i < ihi; i++)
+            if (relax_cell(Fh, zt, i, r, eps)) {
+              changed = true;
+              border_changed |= cedge || i == 0 || i == th - 1;
+            }
+        __syncthreads();
+        if (cin)
+          for (int i = ihi - 1; i >= ilo; i--)
+            if (relax_cell(Fh, zt, i, r, eps)) {
+              changed = true;
+              border_changed |= cedge || i == 0 || i == th - 1;
+            }
+        tile_changed |= changed;
+        if (!__syncthreads_or(changed)) {
+          settled_now = true;
+          break;
+        }
+      }
     }
     const bool tile_any = __syncthreads_or(tile_changed);
     const bool border_any = __syncthreads_or(border_changed);
@@ -169,7 +236,7 @@ __global__ void __launch_bounds__(NTF) k_fill_round(const float* z, int64_t H, i
           marked++;
         }
       }
-      if (wave >= MAX_WAVES) {  // not settled within the cap: visit it again, every cell
+      if (!settled_now) {  // not settled within the caps: visit it again, every cell
         act_next[t] = 1;
         settled[t] = 0;
         marked++;
