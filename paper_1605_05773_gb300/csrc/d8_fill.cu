@@ -32,7 +32,7 @@ namespace fill {
 constexpr int T = 64;
 constexpr int NTF = 256;
 constexpr int HW = T + 2;               // halo row width
-constexpr int SWEEP_AFTER = 8;          // waves before the tile switches to directional sweeps
+constexpr int SWEEP_AFTER = 2;          // waves before the tile switches to directional sweeps
 constexpr int MAX_SWEEPS = 4 * T;       // sweep passes (four directions each) before giving up
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
