@@ -34,7 +34,6 @@ constexpr int NTF = 256;
 constexpr int HW = T + 2;               // halo row width
 constexpr int SWEEP_AFTER = 2;          // waves before the tile switches to directional sweeps
 constexpr int MAX_SWEEPS = 4 * T;       // sweep passes (four directions each) before giving up
-constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
   static constexpr size_t off_f = 0;                                   // float (T+2)^2: F with halo
